@@ -39,7 +39,10 @@ def build(force: bool = False) -> Path:
 def lib():
     global _lib
     if _lib is None:
-        path = build()
+        # PLDS_ORACLE_SO points the tests at a deliberately broken copy of the
+        # oracle (mutation tests of the pins); normally the source is built here.
+        alt = os.environ.get("PLDS_ORACLE_SO")
+        path = Path(alt) if alt else build()
         L = ctypes.CDLL(str(path))
         P = ctypes.c_void_p
         i32p = ctypes.POINTER(ctypes.c_int32)
