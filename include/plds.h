@@ -1,0 +1,170 @@
+/*
+ * plds.h -- C ABI of the GB300 (sm_103a) parallel level data structure (PLDS).
+ *
+ * The library maintains, for an undirected graph on vertex ids [0, n), the levels
+ * of the PLDS of Liu, Shi, Yu, Dhulipala and Shun (SPAA'22, "Parallel
+ * Batch-Dynamic Algorithms for k-Core Decomposition and Related Graph Problems"),
+ * and from them (2+3/lambda)(1+delta)-approximate coreness estimates, under batches
+ * of edge insertions and deletions.  All state lives in GPU memory; every step of a
+ * batch (preprocessing, adjacency update, counters, level rounds) runs in the
+ * library's own CUDA kernels.
+ *
+ * Conventions for every call:
+ *   - Return value: PLDS_OK (0) or a negative PLDS_E* code.  plds_last_status()
+ *     returns the code of the calling thread's last call.
+ *   - Pointers to caller buffers (edges, out) may be host or device pointers; the
+ *     library detects which.  Device pointers must be valid on the handle's device
+ *     and are used in order on the handle's stream; host pointers are copied
+ *     before the call returns.  The caller keeps ownership of its buffers.
+ *   - Edge arrays are int32[B][2] (u, v pairs, row-major, 8 bytes per edge).
+ *   - A handle is used by one host thread and one stream at a time.
+ *   - After PLDS_ETIMEOUT or PLDS_EDEVICE the handle is poisoned: every further
+ *     call except plds_destroy returns PLDS_EPOISONED.
+ */
+#ifndef PLDS_H
+#define PLDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLDS_OK 0
+#define PLDS_EINVAL (-1)     /* bad argument: n, delta, lambda, an id outside [0,n), NULL */
+#define PLDS_ENOMEM (-2)     /* device memory could not be obtained; state unchanged */
+#define PLDS_ETIMEOUT (-3)   /* a bounded device-side wait expired; handle poisoned */
+#define PLDS_EDEVICE (-4)    /* CUDA reported an error; handle poisoned */
+#define PLDS_EINTERNAL (-5)  /* an internal consistency check failed */
+#define PLDS_EPOISONED (-6)  /* handle unusable after an earlier ETIMEOUT/EDEVICE */
+
+typedef struct plds plds_t;
+
+/* Device allocator used for every allocation of a handle.  alloc returns a device
+ * pointer (NULL on failure) usable on `stream`; free releases it.  Either function
+ * may be called from any library call on the handle's host thread. */
+typedef struct plds_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} plds_allocator;
+
+/* Statistics of the handle's last batch call (counts of the method's own work). */
+typedef struct plds_stats {
+    int64_t submitted;   /* edges passed in */
+    int64_t self_loops;  /* dropped: u == v */
+    int64_t duplicates;  /* dropped: repeated (min,max) key in the batch */
+    int64_t filtered;    /* dropped: insert of a present / delete of an absent edge */
+    int64_t valid;       /* updates applied */
+    int64_t rounds;      /* levels at which at least one vertex moved */
+    int64_t moves;       /* level changes (insert: one level each; delete: one per vertex) */
+    int64_t visits;      /* neighbours scanned by moving vertices (sum of their degrees) */
+    int64_t dl_evals;    /* desire-level computations */
+    int64_t dl_visits;   /* neighbours scanned by desire-level computations */
+    int64_t slots_scanned; /* hash slots read by the level rounds (live + empty + tombstone) */
+    int64_t pool_slots_used;
+    int64_t pool_slots_cap;
+    int64_t device_bytes;  /* device memory currently held by the handle */
+    int64_t pool_grows;    /* adjacency pool reallocations so far */
+    int64_t reserved[5];
+} plds_stats_t;
+
+/* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */
+typedef struct plds_tuning {
+    int32_t thread_max_cap;   /* tables up to this many slots are scanned by one thread */
+    int32_t load_num;         /* a table grows when live+tombstones+incoming > cap*load_num/load_den */
+    int32_t load_den;
+    int32_t block_threads;    /* threads per block of the round kernels (multiple of 32) */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the cooperative kernel */
+    int32_t test_delay_us;    /* testing only: block 0 sleeps this long before its first barrier
+                                 (exercises the bounded waits); 0 in normal use */
+    int32_t reserved[2];
+} plds_tuning;
+
+/*
+ * Create an empty PLDS on the current CUDA device: n vertices on level 0, no edges.
+ * delta > 0 and lambda > 0 are the paper's constants (defaults 0.4 and 3); they are
+ * converted to rationals with denominator 10^6.  Levels per group follow the
+ * paper's Section "Detailed PLDS Algorithm": 4*ceil(log_{1+delta} n) (taken as
+ * 4*max(1,t) with t the smallest integer such that (1+delta)^t >= n), groups 0..t.
+ * Returns NULL on error (plds_last_status() says which).
+ */
+plds_t *plds_create(int32_t n, double delta, double lambda);
+
+/*
+ * As plds_create, plus: levels_per_group (0 = the paper's 4*ceil(log_{1+delta} n);
+ * a positive value overrides it), allocator (NULL = cudaMallocAsync/cudaFreeAsync),
+ * stream (a cudaStream_t; NULL = the legacy default stream), flags (must be 0).
+ */
+plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
+                       const plds_allocator *allocator, void *stream, uint32_t flags);
+
+/*
+ * Apply a batch of edge insertions: Algorithm 1's insertion half, i.e. batch
+ * preprocessing (framework section: drop self-loops, keep one copy per (min,max)
+ * key, drop insertions of edges already present) followed by RebalanceInsertions
+ * (Algorithm 2): levels processed bottom-up, every vertex violating Invariant 1
+ * moves up one level per round.  Ids outside [0,n) reject the whole call with
+ * PLDS_EINVAL before anything changes.  B == 0 is a no-op.  Blocks until done.
+ */
+int plds_batch_insert(plds_t *h, const int32_t *edges, int64_t B);
+
+/*
+ * Apply a batch of edge deletions: preprocessing (drop deletions of absent
+ * edges) followed by RebalanceDeletions (Algorithm 3) with desire-levels
+ * (Definition "Desire-level", computed as Algorithm 4 does: the level closest
+ * below at which Invariant 2 holds).  Each vertex moves at most once, down.
+ * Same error behaviour as plds_batch_insert.
+ */
+int plds_batch_delete(plds_t *h, const int32_t *edges, int64_t B);
+
+/*
+ * Coreness estimate of every vertex (Definition "Coreness Estimate"):
+ * (1+delta)^{max(floor((level+1)/L)-1, 0)} with L the levels per group, and 0 for a
+ * vertex of degree 0.  out: double[n], host or device.
+ */
+int plds_coreness(plds_t *h, double *out);
+
+/* The exponent of the estimate above per vertex (-1 for degree 0).  out: int32[n]. */
+int plds_coreness_exponent(plds_t *h, int32_t *out);
+
+/* Current level of every vertex.  out: int32[n], host or device. */
+int plds_levels(plds_t *h, int32_t *out);
+
+/* deg, up-degree and up*-degree counters (Section "Detailed PLDS Algorithm":
+ * up = neighbours on levels >= level(v), up* = neighbours on levels >= level(v)-1).
+ * Any pointer may be NULL.  Each: int32[n], host or device. */
+int plds_counters(plds_t *h, int32_t *deg, int32_t *up, int32_t *upstar);
+
+/* Statistics of the last batch call. */
+int plds_stats(plds_t *h, plds_stats_t *out);
+
+/* out[4] = {t, levels per group, groups, levels K}. */
+int plds_params(plds_t *h, int32_t *out);
+
+/* Per-group integer thresholds: upmax[i] = floor((2+3/lambda)(1+delta)^i) and
+ * dnmin[i] = ceil((1+delta)^i), both clamped to n (Invariants 1 and 2).
+ * Each array has `groups` entries (out[2] of plds_params).  Host pointers. */
+int plds_tables(plds_t *h, int32_t *upmax, int32_t *dnmin);
+
+/* Use another stream for subsequent calls. */
+int plds_set_stream(plds_t *h, void *stream);
+
+/* Replace tuning knobs (see plds_tuning); results are unaffected. */
+int plds_set_tuning(plds_t *h, const plds_tuning *t);
+
+/* Limit, in nanoseconds, of every device-side wait (grid barrier); 0 = default 20 s.
+ * When a wait runs out the kernel stops, the call returns PLDS_ETIMEOUT. */
+int plds_set_wait_limit(plds_t *h, int64_t ns);
+
+/* Status code of the calling thread's last call. */
+int plds_last_status(void);
+
+/* Free all device memory of the handle. */
+void plds_destroy(plds_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLDS_H */

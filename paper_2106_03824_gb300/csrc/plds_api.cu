@@ -1,0 +1,664 @@
+// Host runtime and C ABI of the GB300 PLDS (declared in include/plds.h).
+//
+// One batch call = one cooperative kernel launch that runs every step of the
+// batch (preprocessing, table growth, adjacency update, counters, level rounds)
+// with grid-wide barriers between steps, followed by one read of the control
+// words.  Device memory comes from the caller's allocator (default:
+// cudaMallocAsync on the handle's stream).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "plds.h"
+#include "plds_device.cuh"
+#include "plds_tables.h"
+
+using namespace pl;
+
+static thread_local int g_last_status = PLDS_OK;
+
+static int set_status(int s) {
+    g_last_status = s;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_batch_grid(const __grid_constant__ GraphCtx g) {
+    extern __shared__ int32_t sh[];
+    GridTeam T{g.ctl, g.wait_limit_ns};
+    run_batch(T, g, sh);
+}
+
+// Coreness estimate (Definition "Coreness Estimate"): exponent
+// max(floor((level+1)/Lg) - 1, 0), or -1 (estimate 0) for degree 0.
+__global__ void k_coreness(const int32_t *__restrict__ level, const int32_t *__restrict__ deg, int32_t n,
+                           int32_t Lg, const double *__restrict__ powtab, double *out_est, int32_t *out_exp) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = -1;
+        if (deg[v] > 0) g = max((level[v] + 1) / Lg - 1, 0);
+        if (out_est) out_est[v] = g < 0 ? 0.0 : powtab[g];
+        if (out_exp) out_exp[v] = g;
+    }
+}
+
+// Pool compaction: new offsets = exclusive prefix sum of table sizes.
+__global__ void k_scan_block_sums(const int32_t *__restrict__ cap, int32_t n, long long *bsum) {
+    __shared__ long long s[32];
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    long long x = v < n ? cap[v] : 0;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_scan_top(long long *bsum, int32_t nb, long long *total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        long long run = 0;
+        for (int i = 0; i < nb; ++i) {
+            long long t = bsum[i];
+            bsum[i] = run;
+            run += t;
+        }
+        *total = run;
+    }
+}
+
+__global__ void k_scan_apply(const int32_t *__restrict__ cap, int32_t n, const long long *bsum, int64_t *newoff) {
+    __shared__ long long s[33];
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    long long x = v < n ? cap[v] : 0, incl = x;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            long long t = s[i];
+            s[i] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    if (v < n) newoff[v] = bsum[blockIdx.x] + s[w] + incl - x;
+}
+
+__global__ void k_pool_copy(const int32_t *__restrict__ oldp, int32_t *__restrict__ newp, int64_t *off,
+                            const int64_t *__restrict__ newoff, const int32_t *__restrict__ cap, int32_t n) {
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int lane = threadIdx.x & 31;
+    for (int64_t v = warp; v < n; v += nw) {
+        int32_t c = cap[v];
+        const int4 *src = reinterpret_cast<const int4 *>(oldp + off[v]);
+        int4 *dst = reinterpret_cast<int4 *>(newp + newoff[v]);
+        for (int j = lane; j < (c >> 2); j += 32) dst[j] = src[j];
+        __syncwarp();
+        if (lane == 0) off[v] = newoff[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct plds {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    plds_allocator alloc{};
+    bool custom_alloc = false;
+    bool poisoned = false;
+    int32_t n = 0;
+    Tables T;
+    plds_tuning tune{};
+    int64_t wait_limit_ns = 20ll * 1000 * 1000 * 1000;
+    int num_sms = 0;
+    int32_t stamp_base = 1;
+    int64_t device_bytes = 0;
+    int64_t pool_grows = 0;
+    plds_stats_t last{};
+    // persistent state
+    DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, inc;
+    DevBuf pool, pool_top, ctl;
+    int64_t pool_cap = 0;
+    // scratch: n-sized
+    DevBuf F[2], M[2], TL[2], P[2], R, bins, levlist, CL[2];
+    int64_t clcap = 0;
+    // scratch: batch-sized
+    DevBuf edges, hset, ukeys, vkeys, touched, S, arena;
+    int64_t bcap = 0, hcap = 0, tcap = 0, arena_cap = 0;
+    Ctl host_ctl{};
+};
+
+static void *dev_alloc(plds *h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (h->custom_alloc) {
+        p = h->alloc.alloc(bytes, (void *)h->stream, h->alloc.ctx);
+    } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+static void dev_free(plds *h, DevBuf &b) {
+    if (!b.p) return;
+    if (h->custom_alloc) h->alloc.free(b.p, b.bytes, (void *)h->stream, h->alloc.ctx);
+    else cudaFreeAsync(b.p, h->stream);
+    h->device_bytes -= (int64_t)b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static bool dev_get(plds *h, DevBuf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return true;
+    dev_free(h, b);
+    b.p = dev_alloc(h, bytes);
+    if (!b.p) return false;
+    b.bytes = bytes ? bytes : 16;
+    h->device_bytes += (int64_t)b.bytes;
+    return true;
+}
+
+template <class T>
+static T *P(DevBuf &b) {
+    return reinterpret_cast<T *>(b.p);
+}
+
+static int cuda_check(plds *h) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->poisoned = true;
+        return PLDS_EDEVICE;
+    }
+    return PLDS_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int64_t pow2_at_least(int64_t x) {
+    int64_t c = 1;
+    while (c < x) c <<= 1;
+    return c;
+}
+
+static void free_all(plds *h) {
+    DevBuf *bufs[] = {&h->upmax, &h->dnmin, &h->powtab, &h->level, &h->deg,   &h->up,    &h->upstar,
+                      &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->inc,   &h->pool,
+                      &h->pool_top, &h->ctl, &h->F[0],  &h->F[1],  &h->M[0],  &h->M[1],  &h->TL[0],
+                      &h->TL[1], &h->P[0],  &h->P[1],   &h->R,     &h->bins,  &h->levlist, &h->CL[0],
+                      &h->CL[1], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena};
+    for (DevBuf *b : bufs) dev_free(h, *b);
+}
+
+static bool alloc_chunk_lists(plds *h) {
+    int64_t need = h->pool_cap / kChunk + (int64_t)h->n + 1024;
+    if (h->clcap >= need) return true;
+    for (int i = 0; i < 2; ++i)
+        if (!dev_get(h, h->CL[i], sizeof(int2) * (size_t)need)) return false;
+    h->clcap = need;
+    return true;
+}
+
+static bool ensure_batch_scratch(plds *h, int64_t B) {
+    if (B <= h->bcap) return true;
+    int64_t bc = std::max<int64_t>(B, 1024);
+    int64_t hc = pow2_at_least(2 * bc);
+    int64_t tc = std::min<int64_t>(2 * bc, (int64_t)h->n);
+    int64_t ac = std::max<int64_t>(2 * bc, 1 << 20);
+    if (!dev_get(h, h->edges, sizeof(int2) * (size_t)bc) || !dev_get(h, h->hset, 8 * (size_t)hc) ||
+        !dev_get(h, h->ukeys, 8 * (size_t)bc) || !dev_get(h, h->vkeys, 8 * (size_t)bc) ||
+        !dev_get(h, h->touched, 4 * (size_t)tc) || !dev_get(h, h->S, 4 * (size_t)tc) ||
+        !dev_get(h, h->arena, 4 * (size_t)ac))
+        return false;
+    h->bcap = bc;
+    h->hcap = hc;
+    h->tcap = tc;
+    h->arena_cap = ac;
+    return true;
+}
+
+static int block_threads(const plds *h) { return h->tune.block_threads > 0 ? h->tune.block_threads : 512; }
+
+static size_t smem_bytes(int threads) {
+    return sizeof(int32_t) * (size_t)(2 * kMaxGroups + 64 + (threads / 32) * kWarpHist);
+}
+
+// Move every table into a new pool laid out back to back, with room for `extra`
+// more slots; the old pool is freed.
+static int grow_pool(plds *h, int64_t extra) {
+    const int threads = 1024;
+    int32_t nb = (int32_t)((h->n + threads - 1) / threads);
+    DevBuf bsum, newoff, total;
+    if (!dev_get(h, bsum, sizeof(long long) * (size_t)(nb + 1)) || !dev_get(h, newoff, 8 * (size_t)h->n) ||
+        !dev_get(h, total, 8)) {
+        dev_free(h, bsum);
+        dev_free(h, newoff);
+        dev_free(h, total);
+        return PLDS_ENOMEM;
+    }
+    k_scan_block_sums<<<nb, threads, 0, h->stream>>>(P<int32_t>(h->cap), h->n, P<long long>(bsum));
+    k_scan_top<<<1, 32, 0, h->stream>>>(P<long long>(bsum), nb, P<long long>(total));
+    k_scan_apply<<<nb, threads, 0, h->stream>>>(P<int32_t>(h->cap), h->n, P<long long>(bsum), P<int64_t>(newoff));
+    long long live = 0;
+    cudaMemcpyAsync(&live, total.p, 8, cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    int rc = cuda_check(h);
+    if (rc) return rc;
+    int64_t want = std::max<int64_t>(h->pool_cap, 2 * (live + extra));
+    want = (want + 3) & ~(int64_t)3;
+    DevBuf np;
+    if (!dev_get(h, np, 4 * (size_t)want)) {
+        dev_free(h, bsum);
+        dev_free(h, newoff);
+        dev_free(h, total);
+        return PLDS_ENOMEM;
+    }
+    k_pool_copy<<<std::max(1, h->num_sms * 8), 256, 0, h->stream>>>(P<int32_t>(h->pool), P<int32_t>(np),
+                                                                     P<int64_t>(h->off), P<int64_t>(newoff),
+                                                                     P<int32_t>(h->cap), h->n);
+    unsigned long long top = (unsigned long long)live;
+    cudaMemcpyAsync(h->pool_top.p, &top, 8, cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    dev_free(h, h->pool);
+    h->pool = np;
+    h->pool_cap = want;
+    h->pool_grows++;
+    dev_free(h, bsum);
+    dev_free(h, newoff);
+    dev_free(h, total);
+    if (!alloc_chunk_lists(h)) return PLDS_ENOMEM;
+    return cuda_check(h);
+}
+
+static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
+    GraphCtx g{};
+    g.n = h->n;
+    g.Lg = h->T.Lg;
+    g.K = h->T.K;
+    g.G = h->T.G;
+    g.op = op;
+    g.stamp_base = h->stamp_base;
+    g.thread_max_cap = h->tune.thread_max_cap > 0 ? h->tune.thread_max_cap : 16;
+    g.load_num = h->tune.load_num > 0 ? h->tune.load_num : 3;
+    g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
+    g.wait_limit_ns = h->wait_limit_ns;
+    g.test_delay_us = h->tune.test_delay_us;
+    g.upmax = P<int32_t>(h->upmax);
+    g.dnmin = P<int32_t>(h->dnmin);
+    g.level = P<int32_t>(h->level);
+    g.deg = P<int32_t>(h->deg);
+    g.up = P<int32_t>(h->up);
+    g.upstar = P<int32_t>(h->upstar);
+    g.off = P<int64_t>(h->off);
+    g.cap = P<int32_t>(h->cap);
+    g.tomb = P<int32_t>(h->tomb);
+    g.stamp = P<int32_t>(h->stamp);
+    g.dlv = P<int32_t>(h->dlv);
+    g.inc = P<int32_t>(h->inc);
+    g.slots = P<int32_t>(h->pool);
+    g.pool_top = P<unsigned long long>(h->pool_top);
+    g.pool_cap = h->pool_cap;
+    g.edges = edges;
+    g.B = B;
+    g.hset = P<unsigned long long>(h->hset);
+    g.hcap = h->hcap;
+    g.ukeys = P<unsigned long long>(h->ukeys);
+    g.vkeys = P<unsigned long long>(h->vkeys);
+    g.touched = P<int32_t>(h->touched);
+    g.S = P<int32_t>(h->S);
+    g.bins = P<int32_t>(h->bins);
+    g.levlist = P<int32_t>(h->levlist);
+    for (int i = 0; i < 2; ++i) {
+        g.F[i] = P<int32_t>(h->F[i]);
+        g.M[i] = P<int4>(h->M[i]);
+        g.TL[i] = P<int32_t>(h->TL[i]);
+        g.CL[i] = P<int2>(h->CL[i]);
+        g.P[i] = P<int4>(h->P[i]);
+    }
+    g.R[0] = g.R[1] = P<int32_t>(h->R);
+    g.clcap = h->clcap;
+    g.arena = P<int32_t>(h->arena);
+    g.arena_cap = h->arena_cap;
+    g.ctl = P<Ctl>(h->ctl);
+    return g;
+}
+
+static int launch_batch(plds *h, const GraphCtx &g) {
+    const int threads = block_threads(h);
+    const size_t smem = smem_bytes(threads);
+    static thread_local bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_batch_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done = true;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_grid, threads, smem);
+    int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : std::min(occ, 2);
+    if (per_sm < 1) return PLDS_EDEVICE;
+    dim3 grid(h->num_sms * per_sm), block(threads);
+    void *args[] = {(void *)&g};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_batch_grid, grid, block, args, smem, h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return PLDS_EDEVICE;
+    }
+    return PLDS_OK;
+}
+
+static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
+    if (!h) return PLDS_EINVAL;
+    if (h->poisoned) return PLDS_EPOISONED;
+    if (B < 0 || (B > 0 && !edges)) return PLDS_EINVAL;
+    std::memset(&h->last, 0, sizeof(h->last));
+    h->last.submitted = B;
+    if (B == 0) return PLDS_OK;
+    cudaSetDevice(h->device);
+    if (!ensure_batch_scratch(h, B)) return PLDS_ENOMEM;
+    const int32_t *dedges = edges;
+    if (!is_device_ptr(edges)) {
+        cudaMemcpyAsync(h->edges.p, edges, sizeof(int32_t) * 2 * (size_t)B, cudaMemcpyHostToDevice, h->stream);
+        dedges = P<int32_t>(h->edges);
+    }
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((int64_t)h->stamp_base + 2 * (int64_t)h->T.K + 8 >= 0x7fffffff) {
+            cudaMemsetAsync(h->stamp.p, 0, sizeof(int32_t) * (size_t)h->n, h->stream);
+            h->stamp_base = 1;
+        }
+        cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream);
+        cudaMemsetAsync(h->hset.p, 0xff, 8 * (size_t)h->hcap, h->stream);
+        if (op == kOpInsert) cudaMemsetAsync(h->bins.p, 0, sizeof(int32_t) * ((size_t)h->T.K + 1), h->stream);
+        GraphCtx g = make_ctx(h, op, dedges, B);
+        h->stamp_base += h->T.K + 2;
+        int rc = launch_batch(h, g);
+        if (rc) return rc;
+        cudaMemcpyAsync(&h->host_ctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            h->poisoned = true;
+            return PLDS_EDEVICE;
+        }
+        const Ctl &c = h->host_ctl;
+        if (c.err == 0) break;
+        if (c.err & kErrTimeout) {
+            h->poisoned = true;
+            return PLDS_ETIMEOUT;
+        }
+        if (c.err & kErrInvalidId) return PLDS_EINVAL;
+        if (c.err == kErrNeedPool && attempt < 3) {
+            rc = grow_pool(h, (int64_t)c.grow_total);
+            if (rc) return rc;
+            continue;
+        }
+        h->poisoned = true;
+        return PLDS_EINTERNAL;
+    }
+    const Ctl &c = h->host_ctl;
+    h->last.self_loops = (int64_t)c.st[kStSelfLoops];
+    h->last.duplicates = B - h->last.self_loops - (int64_t)c.ucount;
+    h->last.filtered = (int64_t)c.st[kStFiltered];
+    h->last.valid = (int64_t)c.vcount;
+    h->last.rounds = (int64_t)c.st[kStRounds];
+    h->last.moves = (int64_t)c.st[kStMoves];
+    h->last.visits = (int64_t)c.st[kStVisits];
+    h->last.dl_evals = (int64_t)c.st[kStDlEvals];
+    h->last.dl_visits = (int64_t)c.st[kStDlVisits];
+    h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
+    return PLDS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
+                       const plds_allocator *allocator, void *stream, uint32_t flags) {
+    if (flags != 0 || (allocator && (!allocator->alloc || !allocator->free))) {
+        set_status(PLDS_EINVAL);
+        return nullptr;
+    }
+    plds *h = new (std::nothrow) plds();
+    if (!h) {
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    if (build_tables(n, delta, lambda, levels_per_group, &h->T) != 0) {
+        delete h;
+        set_status(PLDS_EINVAL);
+        return nullptr;
+    }
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->stream = (cudaStream_t)stream;
+    if (allocator) {
+        h->alloc = *allocator;
+        h->custom_alloc = true;
+    }
+    h->n = n;
+    const size_t N = (size_t)n;
+    const size_t G = (size_t)h->T.G, K = (size_t)h->T.K;
+    h->pool_cap = std::max<int64_t>(1 << 20, 8 * (int64_t)n);
+    bool ok = dev_get(h, h->upmax, 4 * G) && dev_get(h, h->dnmin, 4 * G) && dev_get(h, h->powtab, 8 * G) &&
+              dev_get(h, h->level, 4 * N) && dev_get(h, h->deg, 4 * N) && dev_get(h, h->up, 4 * N) &&
+              dev_get(h, h->upstar, 4 * N) && dev_get(h, h->off, 8 * N) && dev_get(h, h->cap, 4 * N) &&
+              dev_get(h, h->tomb, 4 * N) && dev_get(h, h->stamp, 4 * N) && dev_get(h, h->dlv, 4 * N) &&
+              dev_get(h, h->inc, 4 * N) && dev_get(h, h->pool, 4 * (size_t)h->pool_cap) &&
+              dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->F[0], 4 * N) &&
+              dev_get(h, h->F[1], 4 * N) && dev_get(h, h->M[0], 16 * N) && dev_get(h, h->M[1], 16 * N) &&
+              dev_get(h, h->TL[0], 4 * N) && dev_get(h, h->TL[1], 4 * N) && dev_get(h, h->P[0], 32 * N) &&
+              dev_get(h, h->P[1], 32 * N) && dev_get(h, h->R, 4 * N) && dev_get(h, h->bins, 4 * (K + 1)) &&
+              dev_get(h, h->levlist, 4 * (K + 1)) && alloc_chunk_lists(h);
+    if (!ok) {
+        free_all(h);
+        cudaStreamSynchronize(h->stream);
+        delete h;
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    cudaStream_t s = h->stream;
+    cudaMemcpyAsync(h->upmax.p, h->T.upmax.data(), 4 * G, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->dnmin.p, h->T.dnmin.data(), 4 * G, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->powtab.p, h->T.pow.data(), 8 * G, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(h->level.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->deg.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->up.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->upstar.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->off.p, 0, 8 * N, s);
+    cudaMemsetAsync(h->cap.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->tomb.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->stamp.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->dlv.p, 0xff, 4 * N, s);
+    cudaMemsetAsync(h->inc.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->pool_top.p, 0, 8, s);
+    cudaStreamSynchronize(s);
+    if (cuda_check(h) != PLDS_OK) {
+        free_all(h);
+        delete h;
+        set_status(PLDS_EDEVICE);
+        return nullptr;
+    }
+    set_status(PLDS_OK);
+    return h;
+}
+
+plds_t *plds_create(int32_t n, double delta, double lambda) {
+    return plds_create_ex(n, delta, lambda, 0, nullptr, nullptr, 0);
+}
+
+int plds_batch_insert(plds_t *h, const int32_t *edges, int64_t B) {
+    return set_status(run_op(h, edges, B, kOpInsert));
+}
+
+int plds_batch_delete(plds_t *h, const int32_t *edges, int64_t B) {
+    return set_status(run_op(h, edges, B, kOpDelete));
+}
+
+static int copy_out(plds *h, void *dst, const void *src, size_t bytes) {
+    if (is_device_ptr(dst)) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    else cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return PLDS_EDEVICE;
+    }
+    return PLDS_OK;
+}
+
+static int coreness_impl(plds *h, double *est, int32_t *expo) {
+    if (!h) return PLDS_EINVAL;
+    if (h->poisoned) return PLDS_EPOISONED;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->n;
+    bool est_dev = est && is_device_ptr(est), exp_dev = expo && is_device_ptr(expo);
+    DevBuf tmp_est, tmp_exp;
+    double *de = est_dev ? est : nullptr;
+    int32_t *dx = exp_dev ? expo : nullptr;
+    if (est && !est_dev) {
+        if (!dev_get(h, tmp_est, 8 * N)) return PLDS_ENOMEM;
+        de = P<double>(tmp_est);
+    }
+    if (expo && !exp_dev) {
+        if (!dev_get(h, tmp_exp, 4 * N)) {
+            dev_free(h, tmp_est);
+            return PLDS_ENOMEM;
+        }
+        dx = P<int32_t>(tmp_exp);
+    }
+    int blocks = std::max(1, std::min(h->num_sms * 8, (int)((h->n + 255) / 256)));
+    k_coreness<<<blocks, 256, 0, h->stream>>>(P<int32_t>(h->level), P<int32_t>(h->deg), h->n, h->T.Lg,
+                                              P<double>(h->powtab), de, dx);
+    int rc = cuda_check(h);
+    if (!rc && est && !est_dev) cudaMemcpyAsync(est, de, 8 * N, cudaMemcpyDeviceToHost, h->stream);
+    if (!rc && expo && !exp_dev) cudaMemcpyAsync(expo, dx, 4 * N, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        rc = PLDS_EDEVICE;
+    }
+    dev_free(h, tmp_est);
+    dev_free(h, tmp_exp);
+    return rc;
+}
+
+int plds_coreness(plds_t *h, double *out) {
+    if (!out) return set_status(PLDS_EINVAL);
+    return set_status(coreness_impl(h, out, nullptr));
+}
+
+int plds_coreness_exponent(plds_t *h, int32_t *out) {
+    if (!out) return set_status(PLDS_EINVAL);
+    return set_status(coreness_impl(h, nullptr, out));
+}
+
+int plds_levels(plds_t *h, int32_t *out) {
+    if (!h || !out) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    return set_status(copy_out(h, out, h->level.p, 4 * (size_t)h->n));
+}
+
+int plds_counters(plds_t *h, int32_t *deg, int32_t *up, int32_t *upstar) {
+    if (!h) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    const size_t bytes = 4 * (size_t)h->n;
+    int rc = PLDS_OK;
+    if (deg && !rc) rc = copy_out(h, deg, h->deg.p, bytes);
+    if (up && !rc) rc = copy_out(h, up, h->up.p, bytes);
+    if (upstar && !rc) rc = copy_out(h, upstar, h->upstar.p, bytes);
+    return set_status(rc);
+}
+
+int plds_stats(plds_t *h, plds_stats_t *out) {
+    if (!h || !out) return set_status(PLDS_EINVAL);
+    unsigned long long top = 0;
+    cudaMemcpyAsync(&top, h->pool_top.p, 8, cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    *out = h->last;
+    out->pool_slots_used = (int64_t)top;
+    out->pool_slots_cap = h->pool_cap;
+    out->device_bytes = h->device_bytes;
+    out->pool_grows = h->pool_grows;
+    return set_status(PLDS_OK);
+}
+
+int plds_params(plds_t *h, int32_t *out) {
+    if (!h || !out) return set_status(PLDS_EINVAL);
+    out[0] = h->T.t;
+    out[1] = h->T.Lg;
+    out[2] = h->T.G;
+    out[3] = h->T.K;
+    return set_status(PLDS_OK);
+}
+
+int plds_tables(plds_t *h, int32_t *upmax, int32_t *dnmin) {
+    if (!h) return set_status(PLDS_EINVAL);
+    if (upmax) std::memcpy(upmax, h->T.upmax.data(), 4 * (size_t)h->T.G);
+    if (dnmin) std::memcpy(dnmin, h->T.dnmin.data(), 4 * (size_t)h->T.G);
+    return set_status(PLDS_OK);
+}
+
+int plds_set_stream(plds_t *h, void *stream) {
+    if (!h) return set_status(PLDS_EINVAL);
+    cudaStreamSynchronize(h->stream);
+    h->stream = (cudaStream_t)stream;
+    return set_status(PLDS_OK);
+}
+
+int plds_set_tuning(plds_t *h, const plds_tuning *t) {
+    if (!h || !t) return set_status(PLDS_EINVAL);
+    if (t->block_threads && (t->block_threads % 32 || t->block_threads > 1024)) return set_status(PLDS_EINVAL);
+    if (t->thread_max_cap < 0 || t->load_num < 0 || t->load_den < 0 || t->blocks_per_sm < 0 ||
+        t->test_delay_us < 0 || t->test_delay_us > 10 * 1000 * 1000)
+        return set_status(PLDS_EINVAL);
+    if ((t->load_num > 0) != (t->load_den > 0) || (t->load_num > 0 && (t->load_num * 8 > t->load_den * 7)))
+        return set_status(PLDS_EINVAL);  // a table must keep an empty slot
+    h->tune = *t;
+    return set_status(PLDS_OK);
+}
+
+int plds_set_wait_limit(plds_t *h, int64_t ns) {
+    if (!h || ns < 0) return set_status(PLDS_EINVAL);
+    h->wait_limit_ns = ns > 0 ? ns : 20ll * 1000 * 1000 * 1000;
+    return set_status(PLDS_OK);
+}
+
+int plds_last_status(void) { return g_last_status; }
+
+void plds_destroy(plds_t *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

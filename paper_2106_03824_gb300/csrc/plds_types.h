@@ -1,0 +1,103 @@
+// Internal structures shared by the host runtime and the device code of the GB300
+// PLDS library (not part of the public C ABI).
+#pragma once
+#include <cstdint>
+
+namespace pl {
+
+constexpr int32_t kEmpty = -1;          // hash slot never used since the last rebuild
+constexpr int32_t kTomb = -2;           // hash slot of a deleted neighbour
+constexpr int32_t kMoveFlag = 1 << 30;  // level bit: vertex moved up in the current round
+constexpr int32_t kLevelMask = kMoveFlag - 1;
+constexpr int32_t kInf = 0x7fffffff;
+constexpr int kMaxGroups = 512;        // groups (t+1) supported by the device tables
+constexpr int kWindow = 256;           // desire-level histogram window (levels)
+constexpr int kWarpHist = 512;         // per-warp shared histogram ints (>= kMaxGroups, kWindow)
+
+// device error bits
+enum : int32_t {
+    kErrInvalidId = 1,
+    kErrNeedPool = 2,
+    kErrTimeout = 4,
+    kErrInternal = 8,
+    kErrListOverflow = 16,
+};
+
+// statistics slots (Ctl::st)
+enum : int {
+    kStSubmitted = 0, kStSelfLoops, kStDuplicates, kStFiltered, kStValid, kStRounds, kStMoves,
+    kStVisits, kStDlEvals, kStDlVisits, kStSlotsScanned, kStCount
+};
+
+enum : int32_t { kOpInsert = 0, kOpDelete = 1 };
+
+// Control words of one graph, in device memory.
+struct Ctl {
+    unsigned bar_count;   // grid barrier arrivals
+    unsigned bar_gen;     // grid barrier generation
+    int32_t err;          // kErr* bits
+    int32_t rounds_done;  // loop guard
+    unsigned long long ucount;   // unique canonical keys
+    unsigned long long vcount;   // valid (applied) keys
+    int32_t tcount;              // touched vertices
+    int32_t shrink_used;         // arena ints used by table shrinking
+    unsigned long long grow_total;  // slots requested by growing tables
+    int32_t fcnt[2];      // insertion frontier sizes (by round parity)
+    int32_t mcnt[2];      // movers (by round parity)
+    int32_t tlcnt[2];     // thread-mode movers
+    int32_t clcnt[2];     // chunk items
+    int32_t slevel[2];    // insertion round state: current level
+    int32_t spos[2];      // insertion round state: next entry of the level list
+    int32_t nlev;         // number of distinct initial-candidate levels
+    int32_t pcnt[2];      // deletion pending list sizes
+    int32_t rcnt[2];      // deletion recompute list sizes
+    int32_t nextmin[2];   // deletion: smallest pending desire-level
+    int32_t pad[3];
+    unsigned long long st[kStCount];
+};
+
+// Everything a device routine needs to know about one graph and its current batch.
+struct GraphCtx {
+    int32_t n, Lg, K, G;
+    int32_t op;            // kOpInsert / kOpDelete
+    int32_t stamp_base;    // stamps of this batch are stamp_base + 1 .. stamp_base + K + 1
+    int32_t thread_max_cap;
+    int32_t load_num, load_den;
+    int32_t test_delay_us;
+    int64_t wait_limit_ns;
+    const int32_t *upmax;  // [G]
+    const int32_t *dnmin;  // [G]
+    int32_t *level, *deg, *up, *upstar;   // [n]
+    int64_t *off;          // [n] first slot of the vertex's table in the pool
+    int32_t *cap;          // [n] table size (power of two >= 4, or 0)
+    int32_t *tomb;         // [n] tombstones in the table
+    int32_t *stamp;        // [n] dedupe stamps
+    int32_t *dlv;          // [n] pending desire-level, -1 when none
+    int32_t *inc;          // [n] incoming insertions of the batch
+    int32_t *slots;        // adjacency pool
+    unsigned long long *pool_top;  // slots handed out
+    int64_t pool_cap;
+    // batch input and scratch
+    const int32_t *edges;  // int32[B][2]
+    int64_t B;
+    unsigned long long *hset;  // batch key set, hcap entries (power of two), all ones = empty
+    int64_t hcap;
+    unsigned long long *ukeys;  // unique keys [B]
+    unsigned long long *vkeys;  // valid keys [B]
+    int32_t *touched;      // touched vertices [tcap]
+    int32_t *S;            // candidates sorted by level [tcap]
+    int32_t *bins;         // [K+1] level histogram / offsets
+    int32_t *levlist;      // [K] distinct candidate levels
+    int32_t *F[2];         // insertion frontier [n]
+    int4 *M[2];            // movers {v, aux, cap, -} [n]
+    int32_t *TL[2];        // thread-mode mover indices [n]
+    int2 *CL[2];           // chunk items {mover index, chunk} [clcap]
+    int64_t clcap;
+    int4 *P[2];            // pending {v, dl, -, -} [2n]
+    int32_t *R[2];         // desire-level recompute candidates [n]
+    int32_t *arena;        // table-shrink scratch
+    int64_t arena_cap;
+    Ctl *ctl;
+};
+
+}  // namespace pl

@@ -1,0 +1,230 @@
+"""Python binding of the GB300 PLDS C ABI (include/plds.h).
+
+Argument marshalling only: every step of a batch runs in the library's CUDA
+kernels.  PyTorch supplies device memory (through the caching allocator, when
+requested) and the current CUDA stream.  There is no CPU fallback: if the
+library cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_lib" / "libplds_gb300.so"
+
+PLDS_OK, PLDS_EINVAL, PLDS_ENOMEM, PLDS_ETIMEOUT, PLDS_EDEVICE, PLDS_EINTERNAL, PLDS_EPOISONED = \
+    0, -1, -2, -3, -4, -5, -6
+_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEOUT", -4: "EDEVICE", -5: "EINTERNAL",
+          -6: "EPOISONED"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PldsAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class PldsStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "self_loops", "duplicates", "filtered", "valid", "rounds", "moves", "visits",
+        "dl_evals", "dl_visits", "slots_scanned", "pool_slots_used", "pool_slots_cap", "device_bytes",
+        "pool_grows")] + [("reserved", ctypes.c_int64 * 5)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PldsTuning(ctypes.Structure):
+    _fields_ = [("thread_max_cap", ctypes.c_int32), ("load_num", ctypes.c_int32),
+                ("load_den", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("test_delay_us", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class PldsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: PLDS_{_NAMES.get(code, code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load the in-tree CUDA library (build it first with ``_build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise ImportError(f"PLDS CUDA library not built: {LIB_PATH} is missing "
+                          "(run __graft_entry__.build())")
+    L = ctypes.CDLL(str(LIB_PATH))
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.plds_create.restype = vp
+    L.plds_create.argtypes = [i32, dbl, dbl]
+    L.plds_create_ex.restype = vp
+    L.plds_create_ex.argtypes = [i32, dbl, dbl, i32, ctypes.POINTER(PldsAllocator), vp, ctypes.c_uint32]
+    L.plds_batch_insert.argtypes = [vp, vp, i64]
+    L.plds_batch_delete.argtypes = [vp, vp, i64]
+    L.plds_coreness.argtypes = [vp, vp]
+    L.plds_coreness_exponent.argtypes = [vp, vp]
+    L.plds_levels.argtypes = [vp, vp]
+    L.plds_counters.argtypes = [vp, vp, vp, vp]
+    L.plds_stats.argtypes = [vp, ctypes.POINTER(PldsStats)]
+    L.plds_params.argtypes = [vp, vp]
+    L.plds_tables.argtypes = [vp, vp, vp]
+    L.plds_set_stream.argtypes = [vp, vp]
+    L.plds_set_tuning.argtypes = [vp, ctypes.POINTER(PldsTuning)]
+    L.plds_set_wait_limit.argtypes = [vp, i64]
+    L.plds_last_status.argtypes = []
+    L.plds_destroy.argtypes = [vp]
+    L.plds_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _torch_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _torch_allocator():
+    """Allocator callbacks backed by PyTorch's CUDA caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = PldsAllocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    return a
+
+
+class PLDS:
+    """One graph on the current CUDA device; wraps a plds_t handle."""
+
+    def __init__(self, n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0,
+                 torch_allocator: bool = True, stream=None):
+        L = load()
+        self.n = int(n)
+        self._alloc = _torch_allocator() if torch_allocator else None
+        st = stream if stream is not None else (_torch_stream() if torch_allocator else None)
+        self._h = L.plds_create_ex(self.n, float(delta), float(lam), int(levels_per_group),
+                                   ctypes.byref(self._alloc) if self._alloc else None, st, 0)
+        if not self._h:
+            raise PldsError(L.plds_last_status(), "plds_create_ex")
+        p = np.zeros(4, np.int32)
+        L.plds_params(self._h, _ptr(p))
+        self.t, self.Lg, self.G, self.K = (int(x) for x in p)
+
+    def _check(self, rc, what):
+        if rc != PLDS_OK:
+            raise PldsError(rc, what)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().plds_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- batches ---------------------------------------------------------
+    def insert(self, edges, check=True) -> int:
+        """edges: int32 [B,2] numpy array (host) or torch tensor (host or cuda)."""
+        rc = load().plds_batch_insert(self._h, _ptr(edges), int(edges.shape[0]))
+        if check:
+            self._check(rc, "plds_batch_insert")
+        return rc
+
+    def delete(self, edges, check=True) -> int:
+        rc = load().plds_batch_delete(self._h, _ptr(edges), int(edges.shape[0]))
+        if check:
+            self._check(rc, "plds_batch_delete")
+        return rc
+
+    # -- queries ---------------------------------------------------------
+    def coreness(self, out=None):
+        out = np.zeros(self.n, np.float64) if out is None else out
+        self._check(load().plds_coreness(self._h, _ptr(out)), "plds_coreness")
+        return out
+
+    def coreness_exponent(self, out=None):
+        out = np.zeros(self.n, np.int32) if out is None else out
+        self._check(load().plds_coreness_exponent(self._h, _ptr(out)), "plds_coreness_exponent")
+        return out
+
+    def levels(self, out=None):
+        out = np.zeros(self.n, np.int32) if out is None else out
+        self._check(load().plds_levels(self._h, _ptr(out)), "plds_levels")
+        return out
+
+    def counters(self):
+        d, u, s = (np.zeros(self.n, np.int32) for _ in range(3))
+        self._check(load().plds_counters(self._h, _ptr(d), _ptr(u), _ptr(s)), "plds_counters")
+        return d, u, s
+
+    def stats(self) -> dict:
+        st = PldsStats()
+        self._check(load().plds_stats(self._h, ctypes.byref(st)), "plds_stats")
+        return st.as_dict()
+
+    def tables(self):
+        up = np.zeros(self.G, np.int32)
+        dn = np.zeros(self.G, np.int32)
+        self._check(load().plds_tables(self._h, _ptr(up), _ptr(dn)), "plds_tables")
+        return up, dn
+
+    def set_tuning(self, **kw):
+        t = PldsTuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._check(load().plds_set_tuning(self._h, ctypes.byref(t)), "plds_set_tuning")
+
+    def set_wait_limit(self, ns: int):
+        self._check(load().plds_set_wait_limit(self._h, int(ns)), "plds_set_wait_limit")
+
+    def set_stream(self, stream):
+        self._check(load().plds_set_stream(self._h, stream), "plds_set_stream")
+
+
+def exported_symbols_in_header(header: os.PathLike | None = None):
+    """Function names declared in include/plds.h."""
+    import re
+    header = Path(header) if header else _PKG.parent / "include" / "plds.h"
+    text = header.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(plds_[a-z_]+)\s*\(", text)))
