@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of PLDS batch updates (edge updates/s at batch 1e6) on one GB300.
+
+Workload: R-MAT scale 20, (a,b,c,d) = (.57,.19,.19,.05), edge factor 16,
+symmetrised and deduplicated (~15.7M undirected int32 edges on 2^20 vertices),
+delta = 0.4, lambda = 3.  A step is one batch of 10^6 edge updates through the
+whole hot path (preprocessing, adjacency, counters, level rounds) followed by a
+coreness query of every vertex.  The step stream cycles Ins (all edges from
+empty, shuffled, batches of 10^6) then Del (all edges, a second shuffle).
+The graph state (adjacency pool, level and counter arrays, ~1 GB) is larger
+than L2, so no explicit L2 flush is done between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 (under torchrun) runs N independent replicas (a single graph's level
+rounds do not shard); value = all ranks' updates / max time.
+--impl reference times the sequential CPU oracle on the host cores on bounded
+samples of the same stream.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2106_03824_gb300 import workloads as W  # noqa: E402
+
+METRIC = "edge updates/s at batch 1e6 (Ins/Del/Mix)"
+UNIT = "updates/s"
+
+# dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
+# summarised in profiles/ (kernel source hash at capture time); traffic is
+# reported as null when the kernel source has changed since.
+NCU_TRAFFIC = {"kernel_sha": None, "dram_per_algo_byte": None, "capture": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2106_03824_gb300" / "csrc").iterdir()):
+        if f.suffix in (".cu", ".cuh", ".h", ".cpp"):
+            h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def algo_bytes(s: dict) -> int:
+    """Algorithmic bytes of one batch kernel launch (per-unit figures in the design doc):
+    8 B per submitted edge; 64 B per applied update (2 probes + 2 slot writes of 4 B,
+    6 counter read-modify-writes of 8 B); 4 B per level change + 8 B per neighbour
+    visited by a moving vertex (id + level); 8 B per neighbour visited by a
+    desire-level evaluation."""
+    return (8 * s["submitted"] + 64 * s["valid"] + 4 * s["moves"] + 8 * s["visits"]
+            + 8 * s["dl_visits"])
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_stream(scale: int, batch: int, seed: int = 1):
+    e = W.rmat(scale, 16, seed=seed)
+    ins = W.shuffled(e, 11)
+    dele = W.shuffled(e, 12)
+    steps = [("ins", s, min(s + batch, e.shape[0])) for s in range(0, e.shape[0], batch)]
+    steps += [("del", s, min(s + batch, e.shape[0])) for s in range(0, e.shape[0], batch)]
+    return e, ins, dele, steps
+
+
+def cpu_sample(scale, ins, sample_batch=500_000):
+    """The oracle (as it stands, 1 core) on a bounded prefix of the stream's first batch."""
+    from oracle import oracle as O
+    o = O.OraclePLDS(1 << scale)
+    b = ins[:sample_batch]
+    t0 = time.perf_counter()
+    o.insert(b)
+    dt = time.perf_counter() - t0
+    return {"value": b.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {b.shape[0]} edges of the first Ins batch of the same R-MAT scale-{scale} "
+                      f"stream, applied as one batch to the empty graph ({dt:.1f} s on 1 host core; the "
+                      f"full 10^6-edge batch takes minutes)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    e, ins, dele, steps = make_stream(args.scale, args.batch)
+    from oracle import oracle as O
+    o = O.OraclePLDS(1 << args.scale)
+    b = args.ref_batch
+    pos = 0
+
+    def step():
+        nonlocal pos
+        if pos >= ins.shape[0]:
+            pos = 0
+        chunk = ins[pos:pos + b]
+        o.insert(chunk)
+        pos += chunk.shape[0]
+        return chunk.shape[0]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    upd = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = upd / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"rmat{args.scale}_ef16_ins_del_cycle", "batch": b,
+                       "note": "sequential CPU oracle; each step one Ins batch of the same stream"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} Ins batches of {b} edges after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=29)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=1_000_000)
+    ap.add_argument("--ref-batch", type=int, default=100_000)
+    ap.add_argument("--cpu-batch", type=int, default=500_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_03824_gb300 import plds as P
+
+    e, ins_h, del_h, steps = make_stream(args.scale, args.batch)
+    n = 1 << args.scale
+    ins_d = torch.from_numpy(ins_h).cuda()
+    del_d = torch.from_numpy(del_h).cuda()
+    core_d = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def run_steps(g, k0, count, host=False, pinned=None, core_h=None):
+        upd, recs = 0, []
+        for k in range(k0, k0 + count):
+            kind, a, b = steps[k % len(steps)]
+            if host:
+                src = pinned[kind][a:b]
+            else:
+                src = (ins_d if kind == "ins" else del_d)[a:b]
+            (g.insert if kind == "ins" else g.delete)(src)
+            recs.append(g.stats())
+            g.coreness(core_h if host else core_d)
+            upd += b - a
+        return upd, recs
+
+    g = P.PLDS(n)
+    run_steps(g, 0, args.warmup)
+    launches0 = g.stats()["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        upd, recs = run_steps(g, args.warmup, args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = g.stats()["launches"] - launches0
+    g.close()
+    t_max = ms
+    upd_all = upd
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([float(upd)], device="cuda")
+        dist.all_reduce(u)
+        upd_all = int(u.item())
+    value = upd_all / (t_max / 1e3)
+
+    # roofline of the batch kernel: algorithmic bytes / event-timed kernel duration
+    kern_ns = sum(r["kernel_ns"] for r in recs)
+    abytes = sum(algo_bytes(r) for r in recs)
+    achieved = abytes / (kern_ns / 1e9) / 1e9 if kern_ns else None
+    peak, peak_src = measured_peaks()
+    traffic = None
+    if NCU_TRAFFIC["kernel_sha"] == kernel_sha() and NCU_TRAFFIC["dram_per_algo_byte"]:
+        traffic = NCU_TRAFFIC["dram_per_algo_byte"] * abytes / len(recs)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": "k_batch_grid", "peak_source": peak_src,
+            "kernel_ms_per_launch": kern_ns / 1e6 / len(recs),
+            "algo_bytes_per_launch": abytes / len(recs)}
+
+    # e2e: the same steps through the C ABI with pinned host buffers (H2D of the batch
+    # and D2H of every vertex's coreness inside the timed region), fresh graph
+    e2e = None
+    if not args.no_e2e:
+        pinned = {"ins": torch.from_numpy(ins_h).pin_memory().numpy(),
+                  "del": torch.from_numpy(del_h).pin_memory().numpy()}
+        core_h = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+        g2 = P.PLDS(n)
+        run_steps(g2, 0, args.warmup, host=True, pinned=pinned, core_h=core_h)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upd2, _ = run_steps(g2, args.warmup, args.steps, host=True, pinned=pinned, core_h=core_h)
+        torch.cuda.synchronize()
+        dt2 = time.perf_counter() - t0
+        g2.close()
+        if dist:
+            t = torch.tensor([dt2], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt2 = float(t.item())
+        e2e = {"value": upd2 * world / dt2, "unit": UNIT, "h2d_bytes_per_step": 8 * upd2 / args.steps,
+               "d2h_bytes_per_step": 8 * n}
+
+    phases = {}
+    for kind in ("ins", "del"):
+        sel = [(r, steps[(args.warmup + i) % len(steps)]) for i, r in enumerate(recs)
+               if steps[(args.warmup + i) % len(steps)][0] == kind]
+        if sel:
+            ns = sum(r["kernel_ns"] for r, _ in sel)
+            phases[kind] = {"steps": len(sel), "updates_per_s_kernel": sum(s[2] - s[1] for _, s in sel) / (ns / 1e9)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(args.scale, ins_h, args.cpu_batch)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}_ef16_B{args.batch:.0e}_ins_del_cycle".replace("+0", ""),
+                   "graph": f"R-MAT scale {args.scale}, (.57,.19,.19,.05), edge factor 16, symmetrised, deduplicated",
+                   "n": n, "m": int(e.shape[0]), "batch": args.batch, "delta": 0.4, "lambda": 3,
+                   "stream": "Ins all edges from empty, then Del all edges (cyclic)",
+                   "form": "plain: one synchronous launch sequence per batch",
+                   "l2": "no flush: graph state (~1 GB adjacency + arrays) is larger than the 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "phases": phases,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,7 +67,11 @@ typedef struct plds_stats {
     int64_t pool_slots_cap;
     int64_t device_bytes;  /* device memory currently held by the handle */
     int64_t pool_grows;    /* adjacency pool reallocations so far */
-    int64_t reserved[5];
+    int64_t err_bits;      /* device error word of the last call (diagnostics) */
+    int64_t err_site;      /* internal check that raised it (diagnostics) */
+    int64_t err_info[3];   /* values seen by that check (diagnostics) */
+    int64_t kernel_ns;     /* device time of the last call's batch kernel (CUDA events) */
+    int64_t launches;      /* kernels launched by this handle since creation */
 } plds_stats_t;
 
 /* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */

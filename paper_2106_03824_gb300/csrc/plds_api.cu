@@ -135,6 +135,8 @@ struct plds {
     int64_t device_bytes = 0;
     int64_t pool_grows = 0;
     plds_stats_t last{};
+    int64_t launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // persistent state
     DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, inc;
     DevBuf pool, pool_top, ctl;
@@ -263,6 +265,7 @@ static int grow_pool(plds *h, int64_t extra) {
         dev_free(h, total);
         return PLDS_ENOMEM;
     }
+    h->launches += 4;
     k_scan_block_sums<<<nb, threads, 0, h->stream>>>(P<int32_t>(h->cap), h->n, P<long long>(bsum));
     k_scan_top<<<1, 32, 0, h->stream>>>(P<long long>(bsum), nb, P<long long>(total));
     k_scan_apply<<<nb, threads, 0, h->stream>>>(P<int32_t>(h->cap), h->n, P<long long>(bsum), P<int64_t>(newoff));
@@ -364,7 +367,10 @@ static int launch_batch(plds *h, const GraphCtx &g) {
     if (per_sm < 1) return PLDS_EDEVICE;
     dim3 grid(h->num_sms * per_sm), block(threads);
     void *args[] = {(void *)&g};
+    cudaEventRecord(h->ev0, h->stream);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_batch_grid, grid, block, args, smem, h->stream);
+    cudaEventRecord(h->ev1, h->stream);
+    h->launches++;
     if (e != cudaSuccess) {
         cudaGetLastError();
         h->poisoned = true;
@@ -405,7 +411,15 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
             h->poisoned = true;
             return PLDS_EDEVICE;
         }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last.kernel_ns += (int64_t)(ms * 1e6);
+        cudaGetLastError();
         const Ctl &c = h->host_ctl;
+        h->last.err_bits = c.err;
+        h->last.err_site = c.err_site;
+        h->last.err_info[0] = c.err_info[0];
+        h->last.err_info[1] = c.err_info[1];
+        h->last.err_info[2] = c.err_info[2];
         if (c.err == 0) break;
         if (c.err & kErrTimeout) {
             h->poisoned = true;
@@ -421,6 +435,11 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
         return PLDS_EINTERNAL;
     }
     const Ctl &c = h->host_ctl;
+    h->last.err_bits = c.err;
+    h->last.err_site = c.err_site;
+        h->last.err_info[0] = c.err_info[0];
+        h->last.err_info[1] = c.err_info[1];
+        h->last.err_info[2] = c.err_info[2];
     h->last.self_loops = (int64_t)c.st[kStSelfLoops];
     h->last.duplicates = B - h->last.self_loops - (int64_t)c.ucount;
     h->last.filtered = (int64_t)c.st[kStFiltered];
@@ -456,6 +475,12 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
         return nullptr;
     }
     cudaGetDevice(&h->device);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_status(PLDS_EDEVICE);
+        return nullptr;
+    }
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     h->stream = (cudaStream_t)stream;
     if (allocator) {
@@ -553,6 +578,7 @@ static int coreness_impl(plds *h, double *est, int32_t *expo) {
         dx = P<int32_t>(tmp_exp);
     }
     int blocks = std::max(1, std::min(h->num_sms * 8, (int)((h->n + 255) / 256)));
+    h->launches++;
     k_coreness<<<blocks, 256, 0, h->stream>>>(P<int32_t>(h->level), P<int32_t>(h->deg), h->n, h->T.Lg,
                                               P<double>(h->powtab), de, dx);
     int rc = cuda_check(h);
@@ -605,6 +631,7 @@ int plds_stats(plds_t *h, plds_stats_t *out) {
     out->pool_slots_cap = h->pool_cap;
     out->device_bytes = h->device_bytes;
     out->pool_grows = h->pool_grows;
+    out->launches = h->launches;
     return set_status(PLDS_OK);
 }
 
@@ -657,6 +684,8 @@ void plds_destroy(plds_t *h) {
     cudaStreamSynchronize(h->stream);
     free_all(h);
     cudaStreamSynchronize(h->stream);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
     cudaGetLastError();
     delete h;
 }

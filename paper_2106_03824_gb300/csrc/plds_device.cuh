@@ -219,6 +219,17 @@ __device__ __forceinline__ int32_t next_pow2(int64_t x) {
 
 __device__ __forceinline__ int32_t sid_of(const GraphCtx &g, int32_t l) { return g.stamp_base + 1 + l; }
 
+// Record an error bit and, for the first error only, which check raised it.
+__device__ __forceinline__ void report(const GraphCtx &g, int32_t bit, int32_t site, int32_t a = 0,
+                                      int32_t b = 0, int32_t c = 0) {
+    if (atomicCAS(&g.ctl->err_site, 0, site) == 0) {
+        g.ctl->err_info[0] = a;
+        g.ctl->err_info[1] = b;
+        g.ctl->err_info[2] = c;
+    }
+    atomicOr(&g.ctl->err, bit);
+}
+
 // ---------------------------------------------------------------------------
 // Block-level exclusive scan used by the candidate sort (block 0 of the team).
 // ---------------------------------------------------------------------------
@@ -385,7 +396,7 @@ __device__ void step_apply_insert(Team &T, const GraphCtx &g) {
         int32_t lu = g.level[u], lv = g.level[v];
         int ru = table_insert(g.slots, g.off[u], g.cap[u], v);
         int rv = table_insert(g.slots, g.off[v], g.cap[v], u);
-        if (ru < 0 || rv < 0) atomicOr(&g.ctl->err, kErrInternal);
+        if (ru < 0 || rv < 0) report(g, kErrInternal, 1, ru < 0 ? u : v, g.cap[ru < 0 ? u : v], g.deg[ru < 0 ? u : v]);
         if (ru == 1) atomicSub(&g.tomb[u], 1);
         if (rv == 1) atomicSub(&g.tomb[v], 1);
         atomicAdd(&g.deg[u], 1);
@@ -407,7 +418,7 @@ __device__ void step_apply_delete(Team &T, const GraphCtx &g) {
         int32_t lu = g.level[u], lv = g.level[v];
         bool eu = table_erase(g.slots, g.off[u], g.cap[u], v);
         bool ev = table_erase(g.slots, g.off[v], g.cap[v], u);
-        if (!eu || !ev) atomicOr(&g.ctl->err, kErrInternal);
+        if (!eu || !ev) report(g, kErrInternal, 2);
         atomicAdd(&g.tomb[u], 1);
         atomicAdd(&g.tomb[v], 1);
         atomicSub(&g.deg[u], 1);
@@ -434,7 +445,8 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
             c = g.cap[x];
             int32_t tb = g.tomb[x];
             if (c > 4 && ((int64_t)d * 8 < c || (int64_t)tb * 4 > c)) {
-                nc = next_pow2(2 * (int64_t)d);
+                // rebuilt in place, so never larger than the current region (d < c always)
+                nc = min(next_pow2(2 * (int64_t)d), c);
                 want = nc < c || tb > 0;
             }
         }
@@ -469,7 +481,7 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
                 written += tot;
             }
             if (written != sd) {  // counters and table disagree: report, keep the table
-                if (lane_id() == 0) atomicOr(&g.ctl->err, kErrInternal);
+                if (lane_id() == 0) report(g, kErrInternal, 3);
                 continue;
             }
             __syncwarp();
@@ -508,7 +520,7 @@ __device__ __forceinline__ void enqueue_mover(Team &T, const GraphCtx &g, int pa
         if (lane_id() == 0) base = atomicAdd(&g.ctl->clcnt[par], tot);
         base = __shfl_sync(kFull, base, 0);
         if ((int64_t)base + tot > g.clcap) {
-            if (lane_id() == 0) atomicOr(&g.ctl->err, kErrListOverflow);
+            if (lane_id() == 0) report(g, kErrListOverflow, 4, base, tot, (int32_t)g.clcap);
         } else {
             for (int k = 0; k < nch; ++k) g.CL[par][base + ex + k] = make_int2(mi, k);
         }
@@ -591,7 +603,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
         if (sl < l) l = sl;
         if (l == kInf) break;
         if (l >= g.K - 1 || r > g.K + 2) {  // the top group is never violated
-            if (T.leader()) atomicOr(&g.ctl->err, kErrInternal);
+            if (T.leader()) report(g, kErrInternal, 5, l, r, fc);
             return false;
         }
         int32_t s_lo = 0, s_hi = 0;
@@ -618,14 +630,17 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
                 if (i < fc) {
                     v = g.F[p][i];
                 } else {
+                    // skip if v is also in F: F entries carry scur, or snext once their
+                    // copy has already moved v in this phase
                     v = g.S[s_lo + (i - fc)];
-                    valid = atomicExch(&g.stamp[v], scur) != scur;  // not already in F
+                    const int32_t old = atomicExch(&g.stamp[v], scur);
+                    valid = old != scur && old != snext;
                 }
             }
             if (valid) {
                 int32_t raw = g.level[v];
                 if ((raw & kLevelMask) != l) {
-                    atomicOr(&g.ctl->err, kErrInternal);
+                    report(g, kErrInternal, 6, v, raw, l);
                 } else {
                     upv = g.up[v];
                     mover = upv > cut;  // Invariant 1 violated on level l
@@ -854,7 +869,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
         const int32_t l = g.ctl->nextmin[p];
         if (l == kInf) break;
         if (r > g.K + 2) {
-            if (T.leader()) atomicOr(&g.ctl->err, kErrInternal);
+            if (T.leader()) report(g, kErrInternal, 7);
             return false;
         }
         const int32_t sid = sid_of(g, l);
@@ -983,7 +998,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
                     evals++;
                     evisits += g.deg[sw];
                     if (d <= l) {
-                        atomicOr(&g.ctl->err, kErrInternal);
+                        report(g, kErrInternal, 8);
                     } else if (d != g.dlv[sw]) {
                         g.dlv[sw] = d;
                         int pos = atomicAdd(&g.ctl->pcnt[q], 1);

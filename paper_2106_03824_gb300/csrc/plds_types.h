@@ -52,7 +52,9 @@ struct Ctl {
     int32_t pcnt[2];      // deletion pending list sizes
     int32_t rcnt[2];      // deletion recompute list sizes
     int32_t nextmin[2];   // deletion: smallest pending desire-level
-    int32_t pad[3];
+    int32_t err_site;     // which check raised the first error (0 = none)
+    int32_t err_info[3];  // values seen by that check (diagnostics)
+    int32_t pad[2];
     unsigned long long st[kStCount];
 };
 

@@ -33,10 +33,13 @@ class PldsStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "submitted", "self_loops", "duplicates", "filtered", "valid", "rounds", "moves", "visits",
         "dl_evals", "dl_visits", "slots_scanned", "pool_slots_used", "pool_slots_cap", "device_bytes",
-        "pool_grows")] + [("reserved", ctypes.c_int64 * 5)]
+        "pool_grows", "err_bits", "err_site")] + [("err_info", ctypes.c_int64 * 3)] + \
+        [(k, ctypes.c_int64) for k in ("kernel_ns", "launches")]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "err_info"}
+        d["err_info"] = [int(x) for x in self.err_info]
+        return d
 
 
 class PldsTuning(ctypes.Structure):
@@ -92,7 +95,7 @@ def _ptr(x):
     """Data pointer of a torch tensor or numpy array (must be contiguous)."""
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
-            raise ValueError("array must be C-contiguous")
+            raise ValueError("array must be C-contiguous (np.ascontiguousarray)")
         return ctypes.c_void_p(x.ctypes.data)
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
@@ -163,14 +166,24 @@ class PLDS:
         self.close()
 
     # -- batches ---------------------------------------------------------
+    @staticmethod
+    def _edges(edges):
+        if isinstance(edges, np.ndarray):
+            return np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        if edges.dtype != __import__("torch").int32 or not edges.is_contiguous():
+            raise ValueError("edge tensor must be contiguous int32 [B,2]")
+        return edges
+
     def insert(self, edges, check=True) -> int:
         """edges: int32 [B,2] numpy array (host) or torch tensor (host or cuda)."""
+        edges = self._edges(edges)
         rc = load().plds_batch_insert(self._h, _ptr(edges), int(edges.shape[0]))
         if check:
             self._check(rc, "plds_batch_insert")
         return rc
 
     def delete(self, edges, check=True) -> int:
+        edges = self._edges(edges)
         rc = load().plds_batch_delete(self._h, _ptr(edges), int(edges.shape[0]))
         if check:
             self._check(rc, "plds_batch_delete")
