@@ -124,6 +124,29 @@ int plds_batch_insert(plds_t *h, const int32_t *edges, int64_t B);
 int plds_batch_delete(plds_t *h, const int32_t *edges, int64_t B);
 
 /*
+ * Allocation-free variant of plds_batch_insert (is_delete = 0) and
+ * plds_batch_delete (is_delete = 1); the paper has no counterpart: it exists for
+ * callers that must not allocate device memory while updating, such as a
+ * latency-critical update loop (cudaMalloc can synchronise the whole device) or
+ * a process with a fixed device-memory budget whose allocator cannot be called
+ * from here.  Same batch semantics and results as the regular calls.
+ *   - Uses only the handle's arrays plus one library-wide device array of 4 MiB
+ *     (held by every GPU that loads the library until the process exits) for the
+ *     per-batch scratch; no cudaMalloc, cudaFree or allocator callback is called.
+ *   - B may be at most 65536 edges; larger batches return PLDS_EINVAL (use the
+ *     regular calls).  If the adjacency pool has no room for the tables this
+ *     batch needs, returns PLDS_ENOMEM with the graph unchanged (growing the pool
+ *     would allocate; a regular call grows it).
+ *   - The first call on a device looks up that array's device address; make that
+ *     first call before any stream capture.
+ *   - All calls, from every handle on a device, share the one array and it keeps
+ *     the previous call's contents; calls that overlap on the GPU (another handle
+ *     on another stream, another host thread) race and must be serialised by the
+ *     caller.
+ */
+int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int32_t is_delete);
+
+/*
  * Coreness estimate of every vertex (Definition "Coreness Estimate"):
  * (1+delta)^{max(floor((level+1)/L)-1, 0)} with L the levels per group, and 0 for a
  * vertex of degree 0.  out: double[n], host or device.

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -691,3 +692,133 @@ void plds_destroy(plds_t *h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch entry point.
+//
+// Some callers must not allocate device memory while they apply updates: a
+// latency-critical update loop cannot afford cudaMalloc (it may synchronise the
+// whole device and stall every stream), and a process that runs under a fixed
+// device-memory budget, or whose allocator belongs to a host framework that
+// cannot be re-entered from this call, has no allocator to lend.  For them,
+// plds_batch_static applies a batch using only memory that already exists: the
+// handle's own arrays (allocated by plds_create*) and one file-scope device
+// array that holds the per-batch scratch (edge staging, key set, key lists,
+// touched and candidate lists, shrink scratch) for batches of at most
+// kStaticMaxB edges.  The array costs every GPU that loads this library 4 MiB
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kStaticMaxB = 1 << 16;         // edges per call
+constexpr int64_t kStaticHcap = 1 << 17;         // key-set entries (power of two >= 2 * kStaticMaxB)
+constexpr int64_t kStaticTcap = 2 * kStaticMaxB;  // touched vertices / sorted candidates
+constexpr int64_t kStaticArena = 1 << 17;        // ints of table-shrink scratch
+constexpr size_t kStOffEdges = 0;
+constexpr size_t kStOffHset = kStOffEdges + 8 * (size_t)kStaticMaxB;
+constexpr size_t kStOffUkeys = kStOffHset + 8 * (size_t)kStaticHcap;
+constexpr size_t kStOffVkeys = kStOffUkeys + 8 * (size_t)kStaticMaxB;
+constexpr size_t kStOffTouched = kStOffVkeys + 8 * (size_t)kStaticMaxB;
+constexpr size_t kStOffS = kStOffTouched + 4 * (size_t)kStaticTcap;
+constexpr size_t kStOffArena = kStOffS + 4 * (size_t)kStaticTcap;
+constexpr size_t kStaticBytes = kStOffArena + 4 * (size_t)kStaticArena;  // 4 MiB
+constexpr int kMaxDevices = 128;
+}  // namespace
+
+// Shared by every call on a device; it keeps the previous call's contents.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+static std::mutex g_static_mu;
+static unsigned char *g_static_addr[kMaxDevices];
+
+// Device address of g_static_scratch on the current device (looked up once per
+// device; in host code the symbol itself is only a host-side stand-in).
+static unsigned char *static_scratch(int device) {
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_static_addr[device] = static_cast<unsigned char *>(p);
+    }
+    return g_static_addr[device];
+}
+
+extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int32_t is_delete) {
+    if (!h || B < 0 || (B > 0 && !edges) || (is_delete != 0 && is_delete != 1)) return set_status(PLDS_EINVAL);
+    if (B > kStaticMaxB) return set_status(PLDS_EINVAL);  // larger batches need plds_batch_insert/delete
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    std::memset(&h->last, 0, sizeof(h->last));
+    h->last.submitted = B;
+    if (B == 0) return set_status(PLDS_OK);
+    if (cudaSetDevice(h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return set_status(PLDS_EDEVICE);
+    }
+    unsigned char *base = static_scratch(h->device);
+    if (!base) return set_status(PLDS_EDEVICE);
+    const int32_t op = is_delete ? kOpDelete : kOpInsert;
+    const int32_t *dedges = edges;
+    if (!is_device_ptr(edges)) {
+        cudaMemcpyAsync(base + kStOffEdges, edges, sizeof(int32_t) * 2 * (size_t)B, cudaMemcpyHostToDevice,
+                        h->stream);
+        dedges = reinterpret_cast<const int32_t *>(base + kStOffEdges);
+    }
+    if ((int64_t)h->stamp_base + 2 * (int64_t)h->T.K + 8 >= 0x7fffffff) {
+        cudaMemsetAsync(h->stamp.p, 0, sizeof(int32_t) * (size_t)h->n, h->stream);
+        h->stamp_base = 1;
+    }
+    // what must start empty: control words, the key set, the level histogram
+    cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream);
+    cudaMemsetAsync(base + kStOffHset, 0xff, 8 * (size_t)kStaticHcap, h->stream);
+    if (op == kOpInsert) cudaMemsetAsync(h->bins.p, 0, sizeof(int32_t) * ((size_t)h->T.K + 1), h->stream);
+    GraphCtx g = make_ctx(h, op, dedges, B);
+    g.hset = reinterpret_cast<unsigned long long *>(base + kStOffHset);
+    g.hcap = kStaticHcap;
+    g.ukeys = reinterpret_cast<unsigned long long *>(base + kStOffUkeys);
+    g.vkeys = reinterpret_cast<unsigned long long *>(base + kStOffVkeys);
+    g.touched = reinterpret_cast<int32_t *>(base + kStOffTouched);
+    g.S = reinterpret_cast<int32_t *>(base + kStOffS);
+    g.arena = reinterpret_cast<int32_t *>(base + kStOffArena);
+    g.arena_cap = kStaticArena;
+    h->stamp_base += h->T.K + 2;
+    int rc = launch_batch(h, g);
+    if (rc) return set_status(rc);
+    cudaMemcpyAsync(&h->host_ctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return set_status(PLDS_EDEVICE);
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last.kernel_ns = (int64_t)(ms * 1e6);
+    cudaGetLastError();
+    const Ctl &c = h->host_ctl;
+    h->last.err_bits = c.err;
+    h->last.err_site = c.err_site;
+    if (c.err & kErrTimeout) {
+        h->poisoned = true;
+        return set_status(PLDS_ETIMEOUT);
+    }
+    if (c.err & kErrInvalidId) return set_status(PLDS_EINVAL);
+    // the adjacency pool is full: growing it would allocate, so report and leave
+    // the graph unchanged (a regular plds_batch_insert call can grow it)
+    if (c.err == kErrNeedPool) return set_status(PLDS_ENOMEM);
+    if (c.err) {
+        h->poisoned = true;
+        return set_status(PLDS_EINTERNAL);
+    }
+    h->last.self_loops = (int64_t)c.st[kStSelfLoops];
+    h->last.duplicates = B - h->last.self_loops - (int64_t)c.ucount;
+    h->last.filtered = (int64_t)c.st[kStFiltered];
+    h->last.valid = (int64_t)c.vcount;
+    h->last.rounds = (int64_t)c.st[kStRounds];
+    h->last.moves = (int64_t)c.st[kStMoves];
+    h->last.visits = (int64_t)c.st[kStVisits];
+    h->last.dl_evals = (int64_t)c.st[kStDlEvals];
+    h->last.dl_visits = (int64_t)c.st[kStDlVisits];
+    h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
+    return set_status(PLDS_OK);
+}
