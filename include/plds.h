@@ -79,11 +79,12 @@ typedef struct plds_tuning {
     int32_t thread_max_cap;   /* tables up to this many slots are scanned by one thread */
     int32_t load_num;         /* a table grows when live+tombstones+incoming > cap*load_num/load_den */
     int32_t load_den;
-    int32_t block_threads;    /* threads per block of the round kernels (multiple of 32) */
+    int32_t block_threads;    /* threads per block of the batch kernel (multiple of 32, 128..512) */
     int32_t blocks_per_sm;    /* resident blocks per SM for the cooperative kernel */
     int32_t test_delay_us;    /* testing only: block 0 sleeps this long before its first barrier
                                  (exercises the bounded waits); 0 in normal use */
-    int32_t reserved[2];
+    int32_t trace_rounds;     /* diagnostics: 1 = record one line per level round (plds_trace) */
+    int32_t barrier_sleep_ns; /* pause between polls of a grid-barrier wait (0 = default 32, -1 = none) */
 } plds_tuning;
 
 /*
@@ -184,6 +185,15 @@ int plds_set_tuning(plds_t *h, const plds_tuning *t);
 /* Limit, in nanoseconds, of every device-side wait (grid barrier); 0 = default 20 s.
  * When a wait runs out the kernel stops, the call returns PLDS_ETIMEOUT. */
 int plds_set_wait_limit(plds_t *h, int64_t ns);
+
+/* Diagnostics: per-round records of the last batch call when tuning.trace_rounds
+ * is set.  Each record is 12 int32: {level, candidates (insert) or pending entries
+ * (delete), movers, thread-mode movers, chunk items, then nanoseconds seen by the
+ * first block: insert {phase A work, phase A publish + barrier, phase B work,
+ * phase B publish + barrier}, delete {phase 1, phase 2, phase 3}; rest 0}.
+ * out holds cap records;
+ * returns the number of records written, or a negative PLDS_E* code. */
+int plds_trace(plds_t *h, int32_t *out, int32_t cap);
 
 /* Status code of the calling thread's last call. */
 int plds_last_status(void);

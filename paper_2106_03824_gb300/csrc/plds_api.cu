@@ -30,9 +30,9 @@ static int set_status(int s) {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_batch_grid(const __grid_constant__ GraphCtx g) {
+__global__ void __launch_bounds__(512) k_batch_grid(const __grid_constant__ GraphCtx g) {
     extern __shared__ int32_t sh[];
-    GridTeam T{g.ctl, g.wait_limit_ns};
+    GridTeam T{g.ctl, g.wait_limit_ns, g.barrier_sleep_ns};
     run_batch(T, g, sh);
 }
 
@@ -143,10 +143,10 @@ struct plds {
     DevBuf pool, pool_top, ctl;
     int64_t pool_cap = 0;
     // scratch: n-sized
-    DevBuf F[2], M[2], TL[2], P[2], R, bins, levlist, CL[2];
+    DevBuf F[2], M[2], TL[2], P[2], R, R2, bins, levlist, CL[2];
     int64_t clcap = 0;
     // scratch: batch-sized
-    DevBuf edges, hset, ukeys, vkeys, touched, S, arena;
+    DevBuf edges, hset, ukeys, vkeys, touched, S, arena, trace;
     int64_t bcap = 0, hcap = 0, tcap = 0, arena_cap = 0;
     Ctl host_ctl{};
 };
@@ -215,8 +215,8 @@ static void free_all(plds *h) {
     DevBuf *bufs[] = {&h->upmax, &h->dnmin, &h->powtab, &h->level, &h->deg,   &h->up,    &h->upstar,
                       &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->inc,   &h->pool,
                       &h->pool_top, &h->ctl, &h->F[0],  &h->F[1],  &h->M[0],  &h->M[1],  &h->TL[0],
-                      &h->TL[1], &h->P[0],  &h->P[1],   &h->R,     &h->bins,  &h->levlist, &h->CL[0],
-                      &h->CL[1], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena};
+                      &h->TL[1], &h->P[0],  &h->P[1],   &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0],
+                      &h->CL[1], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace};
     for (DevBuf *b : bufs) dev_free(h, *b);
 }
 
@@ -224,7 +224,7 @@ static bool alloc_chunk_lists(plds *h) {
     int64_t need = h->pool_cap / kChunk + (int64_t)h->n + 1024;
     if (h->clcap >= need) return true;
     for (int i = 0; i < 2; ++i)
-        if (!dev_get(h, h->CL[i], sizeof(int2) * (size_t)need)) return false;
+        if (!dev_get(h, h->CL[i], sizeof(int4) * (size_t)need)) return false;
     h->clcap = need;
     return true;
 }
@@ -250,7 +250,7 @@ static bool ensure_batch_scratch(plds *h, int64_t B) {
 static int block_threads(const plds *h) { return h->tune.block_threads > 0 ? h->tune.block_threads : 512; }
 
 static size_t smem_bytes(int threads) {
-    return sizeof(int32_t) * (size_t)(2 * kMaxGroups + 64 + (threads / 32) * kWarpHist);
+    return sizeof(int32_t) * (size_t)(2 * kMaxGroups + 64 + kWarpHist + 32 + (threads / 32) * kWarpHist + kStageInts);
 }
 
 // Move every table into a new pool laid out back to back, with room for `extra`
@@ -277,6 +277,12 @@ static int grow_pool(plds *h, int64_t extra) {
     if (rc) return rc;
     int64_t want = std::max<int64_t>(h->pool_cap, 2 * (live + extra));
     want = (want + 3) & ~(int64_t)3;
+    if (want / 4 >= ((int64_t)1 << 31)) {  // scan items address the pool in int32 units of 4 slots
+        dev_free(h, bsum);
+        dev_free(h, newoff);
+        dev_free(h, total);
+        return PLDS_ENOMEM;
+    }
     DevBuf np;
     if (!dev_get(h, np, 4 * (size_t)want)) {
         dev_free(h, bsum);
@@ -314,6 +320,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
     g.wait_limit_ns = h->wait_limit_ns;
     g.test_delay_us = h->tune.test_delay_us;
+    g.barrier_sleep_ns = h->tune.barrier_sleep_ns == 0 ? 32 : (h->tune.barrier_sleep_ns < 0 ? 0 : h->tune.barrier_sleep_ns);
     g.upmax = P<int32_t>(h->upmax);
     g.dnmin = P<int32_t>(h->dnmin);
     g.level = P<int32_t>(h->level);
@@ -342,14 +349,17 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     for (int i = 0; i < 2; ++i) {
         g.F[i] = P<int32_t>(h->F[i]);
         g.M[i] = P<int4>(h->M[i]);
-        g.TL[i] = P<int32_t>(h->TL[i]);
-        g.CL[i] = P<int2>(h->CL[i]);
+        g.TL[i] = P<int4>(h->TL[i]);
+        g.CL[i] = P<int4>(h->CL[i]);
         g.P[i] = P<int4>(h->P[i]);
     }
-    g.R[0] = g.R[1] = P<int32_t>(h->R);
+    g.R[0] = P<int32_t>(h->R);
+    g.R[1] = P<int32_t>(h->R2);
     g.clcap = h->clcap;
     g.arena = P<int32_t>(h->arena);
     g.arena_cap = h->arena_cap;
+    g.trace = h->tune.trace_rounds ? P<int32_t>(h->trace) : nullptr;
+    g.trace_cap = h->tune.trace_rounds ? (int32_t)(h->trace.bytes / 48) : 0;
     g.ctl = P<Ctl>(h->ctl);
     return g;
 }
@@ -364,7 +374,7 @@ static int launch_batch(plds *h, const GraphCtx &g) {
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_grid, threads, smem);
-    int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : std::min(occ, 2);
+    int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : 1;
     if (per_sm < 1) return PLDS_EDEVICE;
     dim3 grid(h->num_sms * per_sm), block(threads);
     void *args[] = {(void *)&g};
@@ -499,8 +509,8 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
               dev_get(h, h->inc, 4 * N) && dev_get(h, h->pool, 4 * (size_t)h->pool_cap) &&
               dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->F[0], 4 * N) &&
               dev_get(h, h->F[1], 4 * N) && dev_get(h, h->M[0], 16 * N) && dev_get(h, h->M[1], 16 * N) &&
-              dev_get(h, h->TL[0], 4 * N) && dev_get(h, h->TL[1], 4 * N) && dev_get(h, h->P[0], 32 * N) &&
-              dev_get(h, h->P[1], 32 * N) && dev_get(h, h->R, 4 * N) && dev_get(h, h->bins, 4 * (K + 1)) &&
+              dev_get(h, h->TL[0], 16 * N) && dev_get(h, h->TL[1], 16 * N) && dev_get(h, h->P[0], 32 * N) &&
+              dev_get(h, h->P[1], 32 * N) && dev_get(h, h->R, 4 * N) && dev_get(h, h->R2, 4 * N) && dev_get(h, h->bins, 4 * (K + 1)) &&
               dev_get(h, h->levlist, 4 * (K + 1)) && alloc_chunk_lists(h);
     if (!ok) {
         free_all(h);
@@ -661,12 +671,15 @@ int plds_set_stream(plds_t *h, void *stream) {
 
 int plds_set_tuning(plds_t *h, const plds_tuning *t) {
     if (!h || !t) return set_status(PLDS_EINVAL);
-    if (t->block_threads && (t->block_threads % 32 || t->block_threads > 1024)) return set_status(PLDS_EINVAL);
+    if (t->block_threads && (t->block_threads % 32 || t->block_threads < 128 || t->block_threads > 512))
+        return set_status(PLDS_EINVAL);
     if (t->thread_max_cap < 0 || t->load_num < 0 || t->load_den < 0 || t->blocks_per_sm < 0 ||
-        t->test_delay_us < 0 || t->test_delay_us > 10 * 1000 * 1000)
+        t->test_delay_us < 0 || t->test_delay_us > 10 * 1000 * 1000 || t->barrier_sleep_ns < -1 ||
+        t->barrier_sleep_ns > 100000)
         return set_status(PLDS_EINVAL);
     if ((t->load_num > 0) != (t->load_den > 0) || (t->load_num > 0 && (t->load_num * 8 > t->load_den * 7)))
         return set_status(PLDS_EINVAL);  // a table must keep an empty slot
+    if (t->trace_rounds && !dev_get(h, h->trace, 48 * ((size_t)h->T.K + 16))) return set_status(PLDS_ENOMEM);
     h->tune = *t;
     return set_status(PLDS_OK);
 }
@@ -675,6 +688,15 @@ int plds_set_wait_limit(plds_t *h, int64_t ns) {
     if (!h || ns < 0) return set_status(PLDS_EINVAL);
     h->wait_limit_ns = ns > 0 ? ns : 20ll * 1000 * 1000 * 1000;
     return set_status(PLDS_OK);
+}
+
+int plds_trace(plds_t *h, int32_t *out, int32_t cap) {
+    if (!h || !out || cap < 0) return set_status(PLDS_EINVAL);
+    if (!h->tune.trace_rounds || !h->trace.p) return set_status(0);
+    int32_t k = std::min<int32_t>(h->host_ctl.trace_n, std::min<int32_t>(cap, (int32_t)(h->trace.bytes / 48)));
+    if (k > 0) cudaMemcpy(out, h->trace.p, 48 * (size_t)k, cudaMemcpyDeviceToHost);
+    set_status(PLDS_OK);
+    return k;
 }
 
 int plds_last_status(void) { return g_last_status; }

@@ -35,6 +35,7 @@ __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(volatile
 struct GridTeam {
     Ctl *ctl;
     int64_t limit_ns;
+    int32_t sleep_ns;
     __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ int nthreads() const { return gridDim.x * blockDim.x; }
     __device__ int wid() const { return tid() >> 5; }
@@ -63,7 +64,7 @@ struct GridTeam {
                         atomicOr(&ctl->err, kErrTimeout);
                         break;
                     }
-                    __nanosleep(32);
+                    if (sleep_ns) __nanosleep(sleep_ns);
                 }
             }
             __threadfence();
@@ -200,6 +201,8 @@ __device__ __forceinline__ bool table_erase(int32_t *slots, int64_t off, int32_t
     }
     return false;
 }
+
+__device__ __forceinline__ int4 empty4() { return make_int4(kEmpty, kEmpty, kEmpty, kEmpty); }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     x ^= x >> 33;
@@ -352,37 +355,72 @@ __device__ void step_grow_request(Team &T, const GraphCtx &g) {
     }
 }
 
-// Second pass (after the pool check): allocate and rehash, one warp per table.
+constexpr int32_t kBigTable = 4096;  // tables above this many slots are rebuilt by a block or the team
+
+// Second pass (after the pool check): allocate and rehash.  Small tables: one
+// warp each.  Large tables (hubs): one block each, so a hub's rebuild is not
+// left to a single warp.
 template <class Team>
-__device__ void step_grow_apply(Team &T, const GraphCtx &g) {
+__device__ bool step_grow_apply(Team &T, const GraphCtx &g) {
     const int32_t gc = g.ctl->mcnt[0];
-    for (int i = T.wid(); i < gc; i += T.nwarps()) {
-        int4 it = g.M[0][i];
-        int32_t x = it.x, nc = it.y;
-        unsigned long long noff = 0;
-        if (lane_id() == 0) noff = atomicAdd(g.pool_top, (unsigned long long)nc);
-        noff = __shfl_sync(kFull, noff, 0);
-        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
-        for (int j = lane_id(); j < (nc >> 2); j += 32) nt[j] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-        __syncwarp();
-        __threadfence_block();
-        int32_t oc = g.cap[x];
-        int64_t oo = g.off[x];
-        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + oo);
-        for (int j = lane_id(); j < (oc >> 2); j += 32) {
-            int4 q = ot[j];
-            if (q.x >= 0) table_insert(g.slots, (int64_t)noff, nc, q.x);
-            if (q.y >= 0) table_insert(g.slots, (int64_t)noff, nc, q.y);
-            if (q.z >= 0) table_insert(g.slots, (int64_t)noff, nc, q.z);
-            if (q.w >= 0) table_insert(g.slots, (int64_t)noff, nc, q.w);
-        }
-        __syncwarp();
-        if (lane_id() == 0) {
-            g.off[x] = (int64_t)noff;
-            g.cap[x] = nc;
-            g.tomb[x] = 0;
+    for (int i = T.tid(); i < gc; i += T.nthreads()) {
+        const int4 it = g.M[0][i];
+        const unsigned long long noff = atomicAdd(g.pool_top, (unsigned long long)it.y);
+        const int4 rec = make_int4(it.x, it.y, (int32_t)(noff & 0xffffffffu), (int32_t)(noff >> 32));
+        g.M[0][i] = rec;
+        if (it.y > kBigTable) {
+            const int b = atomicAdd(&g.ctl->mcnt[1], 1);
+            g.M[1][b] = rec;
         }
     }
+    if (!T.sync()) return false;
+    for (int i = T.wid(); i < gc; i += T.nwarps()) {
+        const int4 it = g.M[0][i];
+        const int32_t x = it.x, nc = it.y;
+        if (nc > kBigTable) continue;
+        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
+        for (int j = lane_id(); j < (nc >> 2); j += 32) nt[j] = empty4();
+        __syncwarp();
+        __threadfence_block();
+        const int32_t oc = g.cap[x];
+        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[x]);
+        for (int j = lane_id(); j < (oc >> 2); j += 32) {
+            const int4 q = ot[j];
+            if (q.x >= 0) table_insert(g.slots, noff, nc, q.x);
+            if (q.y >= 0) table_insert(g.slots, noff, nc, q.y);
+            if (q.z >= 0) table_insert(g.slots, noff, nc, q.z);
+            if (q.w >= 0) table_insert(g.slots, noff, nc, q.w);
+        }
+    }
+    // large tables: one block each (blocks work on different tables in parallel)
+    const int32_t nbig = g.ctl->mcnt[1];
+    for (int b = T.bid(); b < nbig; b += T.nthreads() / blockDim.x) {
+        const int4 it = g.M[1][b];
+        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
+        for (int j = threadIdx.x; j < (it.y >> 2); j += blockDim.x) nt[j] = empty4();
+        __syncthreads();
+        const int32_t oc = g.cap[it.x];
+        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
+        for (int j = threadIdx.x; j < (oc >> 2); j += blockDim.x) {
+            const int4 q = ot[j];
+            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
+            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
+            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
+            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
+        }
+        __syncthreads();
+    }
+    if (!T.sync()) return false;
+    for (int i = T.tid(); i < gc; i += T.nthreads()) {
+        const int4 it = g.M[0][i];
+        g.off[it.x] = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        g.cap[it.x] = it.y;
+        g.tomb[it.x] = 0;
+    }
+    if (T.leader()) g.ctl->mcnt[1] = 0;
+    return true;
 }
 
 // Steps A2+A3 (insert): put both directions into the tables and update deg, up
@@ -432,8 +470,9 @@ __device__ void step_apply_delete(Team &T, const GraphCtx &g) {
 
 // After deletions: rebuild, in place and smaller, tables that became sparse or
 // full of tombstones (speed only; skipped when the scratch arena is full).
+// Small tables: one warp each; large ones (hubs): one block each.
 template <class Team>
-__device__ void step_shrink(Team &T, const GraphCtx &g) {
+__device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
     const int32_t tc = g.ctl->tcount;
     for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
         int i = i0 + lane_id();
@@ -455,7 +494,12 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
             base = atomicAdd(&g.ctl->shrink_used, d);
             if ((int64_t)base + d > g.arena_cap) want = false;
         }
-        unsigned m = __ballot_sync(kFull, want);
+        const bool big = want && c > kBigTable;
+        if (big) {  // a whole block rebuilds it below
+            const int b = atomicAdd(&g.ctl->mcnt[1], 1);
+            g.M[1][b] = make_int4(x, nc, base, d);
+        }
+        unsigned m = __ballot_sync(kFull, want && !big);
         while (m) {
             int src = __ffs(m) - 1;
             m &= m - 1;
@@ -468,7 +512,7 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
             int written = 0;
             for (int j0 = 0; j0 < (sc >> 2); j0 += 32) {
                 int j = j0 + lane_id();
-                int4 q = j < (sc >> 2) ? t4[j] : make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+                int4 q = j < (sc >> 2) ? t4[j] : empty4();
                 int cnt = (q.x >= 0) + (q.y >= 0) + (q.z >= 0) + (q.w >= 0);
                 int tot;
                 int ex = warp_exclusive(cnt, &tot);
@@ -485,7 +529,7 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
                 continue;
             }
             __syncwarp();
-            for (int j = lane_id(); j < (snc >> 2); j += 32) t4[j] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+            for (int j = lane_id(); j < (snc >> 2); j += 32) t4[j] = empty4();
             __syncwarp();
             __threadfence_block();
             for (int j = lane_id(); j < written; j += 32) table_insert(g.slots, off, snc, ar[j]);
@@ -496,35 +540,271 @@ __device__ void step_shrink(Team &T, const GraphCtx &g) {
             }
         }
     }
+    if (!T.sync()) return;
+    const int32_t nbig = g.ctl->mcnt[1];
+    for (int b = T.bid(); b < nbig; b += T.nthreads() / blockDim.x) {
+        const int4 it = g.M[1][b];
+        const int32_t x = it.x, nc = it.y, abase = it.z, d = it.w, c = g.cap[x];
+        const int64_t off = g.off[x];
+        int4 *t4 = reinterpret_cast<int4 *>(g.slots + off);
+        int32_t *ar = g.arena + abase;
+        int written = 0;
+        for (int j0 = 0; j0 < (c >> 2); j0 += blockDim.x) {
+            const int j = j0 + threadIdx.x;
+            const int4 q = j < (c >> 2) ? t4[j] : empty4();
+            const int cnt = (q.x >= 0) + (q.y >= 0) + (q.z >= 0) + (q.w >= 0);
+            int tot;
+            int p = written + block_exclusive(cnt, sh_scan, &tot);
+            if (q.x >= 0 && p < d) ar[p++] = q.x;
+            if (q.y >= 0 && p < d) ar[p++] = q.y;
+            if (q.z >= 0 && p < d) ar[p++] = q.z;
+            if (q.w >= 0 && p < d) ar[p++] = q.w;
+            written += tot;
+        }
+        if (written != d) {
+            if (threadIdx.x == 0) report(g, kErrInternal, 3);
+            continue;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < (nc >> 2); j += blockDim.x) t4[j] = empty4();
+        __syncthreads();
+        for (int j = threadIdx.x; j < written; j += blockDim.x) table_insert(g.slots, off, nc, ar[j]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            g.cap[x] = nc;
+            g.tomb[x] = 0;
+        }
+    }
+    if (T.leader()) g.ctl->mcnt[1] = 0;
 }
 
 // ---------------------------------------------------------------------------
-// Mover scans: every mover's table is read either by one thread (small tables)
-// or by warps in 128-slot chunks (chunks of one large table are spread over all
-// warps of the team).  The callback sees each live neighbour once.
+// Mover scans.  Each moving vertex's table is scanned either by one thread
+// (tables of at most thread_max_cap slots) or in 128-slot chunks, one warp per
+// chunk, the chunks of a large table spread over all warps of the team.  A scan
+// item is self-contained -- {vertex, table size (log2) and chunk, table offset in
+// int4 units, aux} -- so a warp goes from the item straight to the slots and
+// then to the neighbours' levels, with all loads of one step issued together.
 // ---------------------------------------------------------------------------
-template <class Team>
-__device__ __forceinline__ void enqueue_mover(Team &T, const GraphCtx &g, int par, bool is_mover, int32_t v,
-                                              int32_t aux) {
-    int32_t c = is_mover ? g.cap[v] : 0;
-    int mi = warp_append(&g.ctl->mcnt[par], is_mover);
-    if (is_mover) g.M[par][mi] = make_int4(v, aux, c, 0);
-    bool small = is_mover && c <= g.thread_max_cap;
-    int ti = warp_append(&g.ctl->tlcnt[par], small);
-    if (small) g.TL[par][ti] = mi;
-    int nch = (is_mover && !small) ? (c + kChunk - 1) / kChunk : 0;
-    int tot;
-    int ex = warp_exclusive(nch, &tot);
-    int base = 0;
-    if (tot) {
-        if (lane_id() == 0) base = atomicAdd(&g.ctl->clcnt[par], tot);
-        base = __shfl_sync(kFull, base, 0);
-        if ((int64_t)base + tot > g.clcap) {
-            if (lane_id() == 0) report(g, kErrListOverflow, 4, base, tot, (int32_t)g.clcap);
-        } else {
-            for (int k = 0; k < nch; ++k) g.CL[par][base + ex + k] = make_int2(mi, k);
-        }
+
+// ---------------------------------------------------------------------------
+// Block-staged list appends.  Thousands of warps appending to one global list
+// would serialise on its counter (same-address atomics in one L2 slice), so a
+// warp claims room in its block's shared-memory buffer with a shared atomic, and
+// at the end of the phase the block publishes the buffer with one global atomic
+// (stage_flush).  A warp that finds the buffer full appends to the global list
+// directly.  hdr[0] = staged count, hdr[1] = end of the valid staged prefix.
+// ---------------------------------------------------------------------------
+template <class V>
+struct Stage {
+    V *buf;          // shared buffer
+    int32_t *hdr;    // shared {count, valid end}
+    int32_t cap;     // buffer capacity
+    int32_t *gcnt;   // global count
+    V *glist;        // global list
+    int64_t gcap;    // global capacity
+};
+
+// Reserve `cnt` consecutive entries for a warp (called by one lane); returns the
+// position and whether it is in the shared buffer.
+template <class V>
+__device__ __forceinline__ int stage_reserve(const Stage<V> &s, int cnt, bool &shared) {
+    int pos = atomicAdd(&s.hdr[0], cnt);
+    if (pos + cnt <= s.cap) {
+        shared = true;
+        return pos;
     }
+    atomicMin(&s.hdr[1], pos);  // staged entries are valid only below the first overflow
+    shared = false;
+    return atomicAdd(s.gcnt, cnt);
+}
+
+template <class V>
+__device__ __forceinline__ void stage_put(const Stage<V> &s, bool shared, int pos, const V &x) {
+    if (shared) s.buf[pos] = x;
+    else if (pos < s.gcap) s.glist[pos] = x;
+}
+
+// Every lane with pred appends x (one reservation per warp).
+template <class V>
+__device__ __forceinline__ void stage_push(const Stage<V> &s, bool pred, const V &x) {
+    const unsigned m = __ballot_sync(kFull, pred);
+    if (m == 0) return;
+    const int lane = lane_id(), leader = __ffs(m) - 1;
+    int pos = 0;
+    bool sh = false;
+    if (lane == leader) pos = stage_reserve(s, __popc(m), sh);
+    pos = __shfl_sync(kFull, pos, leader);
+    sh = __shfl_sync(kFull, sh, leader);
+    if (pred) stage_put(s, sh, pos + __popc(m & ((1u << lane) - 1u)), x);
+}
+
+// Every lane appends the entries of ws flagged in its mask.
+template <int N>
+__device__ __forceinline__ void stage_push_masked(const Stage<int32_t> &s, unsigned mask, const int32_t (&ws)[N]) {
+    int tot;
+    const int ex = warp_exclusive(__popc(mask), &tot);
+    if (tot == 0) return;
+    int pos = 0;
+    bool sh = false;
+    if (lane_id() == 0) pos = stage_reserve(s, tot, sh);
+    pos = __shfl_sync(kFull, pos, 0) + ex;
+    sh = __shfl_sync(kFull, sh, 0);
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (mask >> k & 1u) stage_put(s, sh, pos++, ws[k]);
+}
+
+// Publish the block's staged entries (all threads of the block call).
+template <class V>
+__device__ __forceinline__ void stage_flush(const GraphCtx &g, const Stage<V> &s, int32_t *tmp) {
+    __syncthreads();
+    const int n = min(s.hdr[0], s.hdr[1]);
+    if (threadIdx.x == 0) {
+        const int base = n > 0 ? atomicAdd(s.gcnt, n) : 0;
+        if ((int64_t)base + n > s.gcap || (int64_t)s.gcnt[0] > s.gcap) report(g, kErrListOverflow, 4, base, n, (int32_t)s.gcap);
+        *tmp = base;
+    }
+    __syncthreads();
+    const int base = *tmp;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (base + i < s.gcap) s.glist[base + i] = s.buf[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s.hdr[0] = 0;
+        s.hdr[1] = s.cap;
+    }
+    __syncthreads();
+}
+
+constexpr int kStageF = 2048, kStageTL = 1024, kStageCL = 2048, kStagePK = 1024;
+// shared ints used by the staging area
+constexpr int kStageInts = 16 + kStageF + 4 * (kStageTL + kStageCL + kStagePK);
+
+// Shared-memory staging of one round: frontier / recompute list, thread-mode and
+// chunk scan items, pending entries, and the block's mover count.
+struct RoundStage {
+    Stage<int32_t> f;
+    Stage<int4> tl, cl, pk;
+    int32_t *movers;  // shared mover count of the block
+    int32_t *bmin;    // shared minimum pending level of the block
+    int32_t *tmp;
+};
+
+// Lay out the staging area (kStageInts ints of shared memory, 16-byte aligned).
+__device__ __forceinline__ RoundStage stage_setup(int32_t *base) {
+    RoundStage st{};
+    int32_t *hdr = base;
+    st.f.buf = base + 16;
+    st.tl.buf = reinterpret_cast<int4 *>(base + 16 + kStageF);
+    st.cl.buf = st.tl.buf + kStageTL;
+    st.pk.buf = st.cl.buf + kStageCL;
+    st.f.hdr = hdr;
+    st.tl.hdr = hdr + 2;
+    st.cl.hdr = hdr + 4;
+    st.pk.hdr = hdr + 6;
+    st.f.cap = kStageF;
+    st.tl.cap = kStageTL;
+    st.cl.cap = kStageCL;
+    st.pk.cap = kStagePK;
+    st.movers = hdr + 8;
+    st.bmin = hdr + 9;
+    st.tmp = hdr + 10;  // 4 ints
+    if (threadIdx.x == 0) {
+        hdr[0] = 0; hdr[1] = kStageF;
+        hdr[2] = 0; hdr[3] = kStageTL;
+        hdr[4] = 0; hdr[5] = kStageCL;
+        hdr[6] = 0; hdr[7] = kStagePK;
+        hdr[8] = 0; hdr[9] = kInf;
+    }
+    __syncthreads();
+    return st;
+}
+
+
+__device__ __forceinline__ void stage_init(int32_t *hdr, int cap) {
+    hdr[0] = 0;
+    hdr[1] = cap;
+}
+
+// Publish the selected lists of a phase (bit 0 f, 1 tl, 2 cl, 3 pk) together:
+// warp k reserves list k's global range, then the block copies all of them.
+// The headers are reset at the end; the next use comes after a team barrier.
+template <class V>
+__device__ __forceinline__ void stage_reserve_global(const GraphCtx &g, const Stage<V> &s, int32_t *base_out) {
+    const int n = min(s.hdr[0], s.hdr[1]);
+    const int base = n > 0 ? atomicAdd(s.gcnt, n) : 0;
+    if ((int64_t)base + n > s.gcap) report(g, kErrListOverflow, 4, base, n, (int32_t)s.gcap);
+    *base_out = base;
+}
+
+template <class V>
+__device__ __forceinline__ void stage_copy_out(const Stage<V> &s, int base) {
+    const int n = min(s.hdr[0], s.hdr[1]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (base + i < s.gcap) s.glist[base + i] = s.buf[i];
+}
+
+__device__ __forceinline__ void stage_flush_round(const GraphCtx &g, const RoundStage &st, unsigned which) {
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        if (w == 0 && (which & 1u)) stage_reserve_global(g, st.f, st.tmp + 0);
+        if (w == 1 && (which & 2u)) stage_reserve_global(g, st.tl, st.tmp + 1);
+        if (w == 2 && (which & 4u)) stage_reserve_global(g, st.cl, st.tmp + 2);
+        if (w == 3 && (which & 8u)) stage_reserve_global(g, st.pk, st.tmp + 3);
+    }
+    __syncthreads();
+    if (which & 1u) stage_copy_out(st.f, st.tmp[0]);
+    if (which & 2u) stage_copy_out(st.tl, st.tmp[1]);
+    if (which & 4u) stage_copy_out(st.cl, st.tmp[2]);
+    if (which & 8u) stage_copy_out(st.pk, st.tmp[3]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (which & 1u) { st.f.hdr[0] = 0; st.f.hdr[1] = st.f.cap; }
+        if (which & 2u) { st.tl.hdr[0] = 0; st.tl.hdr[1] = st.tl.cap; }
+        if (which & 4u) { st.cl.hdr[0] = 0; st.cl.hdr[1] = st.cl.cap; }
+        if (which & 8u) { st.pk.hdr[0] = 0; st.pk.hdr[1] = st.pk.cap; }
+    }
+}
+
+// Queue the scan of a mover's table; wsm: 160 ints of per-warp shared scratch.
+__device__ __forceinline__ void enqueue_mover(const GraphCtx &g, const RoundStage &st, bool is_mover, int32_t v,
+                                              int32_t aux, int32_t c, int64_t off, int32_t *wsm) {
+    const int lane = lane_id();
+    const unsigned mm = __ballot_sync(kFull, is_mover);
+    if (mm == 0) return;
+    if (lane == __ffs(mm) - 1) atomicAdd(st.movers, __popc(mm));
+    const int lg = is_mover ? __ffs(c) - 1 : 0;
+    const int32_t goff = (int32_t)(off >> 2);
+    const bool small = is_mover && c <= g.thread_max_cap;
+    stage_push(st.tl, small, make_int4(v, lg, goff, aux));
+    const int nch = (is_mover && !small) ? (c + kChunk - 1) / kChunk : 0;
+    int tot;
+    const int ex = warp_exclusive(nch, &tot);
+    if (tot == 0) return;
+    int pos = 0;
+    bool sh = false;
+    if (lane == 0) pos = stage_reserve(st.cl, tot, sh);
+    pos = __shfl_sync(kFull, pos, 0);
+    sh = __shfl_sync(kFull, sh, 0);
+    // the warp writes all its chunk items together (a large table has many)
+    wsm[lane] = ex;
+    wsm[32 + lane] = v;
+    wsm[64 + lane] = lg;
+    wsm[96 + lane] = goff;
+    wsm[128 + lane] = aux;
+    __syncwarp();
+    for (int t = lane; t < tot; t += 32) {
+        int lo = 0, hi = 31;  // owner: the last lane whose range starts at or before t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (wsm[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        stage_put(st.cl, sh, pos + t,
+                  make_int4(wsm[32 + lo], ((t - wsm[lo]) << 5) | wsm[64 + lo], wsm[96 + lo], wsm[128 + lo]));
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -536,10 +816,13 @@ __device__ __forceinline__ void enqueue_mover(Team &T, const GraphCtx &g, int pa
 template <class Team>
 __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
     const int32_t tc = g.ctl->tcount;
-    for (int i = T.tid(); i < tc; i += T.nthreads()) {
-        int32_t x = g.touched[i];
-        g.inc[x] = 0;
-        atomicAdd(&g.bins[g.level[x]], 1);
+    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
+        const int i = i0 + lane_id();
+        const int32_t x = i < tc ? g.touched[i] : 0;
+        const int32_t lx = i < tc ? g.level[x] : -1;
+        if (i < tc) g.inc[x] = 0;
+        const unsigned peers = __match_any_sync(kFull, lx);  // lanes with the same level add once
+        if (i < tc && lane_id() == __ffs(peers) - 1) atomicAdd(&g.bins[lx], __popc(peers));
     }
     if (T.leader()) {
         g.ctl->mcnt[0] = 0;
@@ -565,35 +848,44 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
         if (threadIdx.x == 0) g.ctl->nlev = runl;
     }
     if (!T.sync()) return false;
-    for (int i = T.tid(); i < tc; i += T.nthreads()) {
-        int32_t x = g.touched[i];
-        int pos = atomicAdd(&g.bins[g.level[x]], 1);
-        g.S[pos] = x;
+    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
+        const int i = i0 + lane_id();
+        const int32_t x = i < tc ? g.touched[i] : 0;
+        const int32_t lx = i < tc ? g.level[x] : -1;
+        const unsigned peers = __match_any_sync(kFull, lx);
+        const int leader = __ffs(peers) - 1;
+        int pos = 0;
+        if (i < tc && lane_id() == leader) pos = atomicAdd(&g.bins[lx], __popc(peers));
+        pos = __shfl_sync(kFull, pos, leader) + __popc(peers & ((1u << lane_id()) - 1u));
+        if (i < tc) g.S[pos] = x;
     }
     // after the scatter bins[l] is the end of level l's range (= start of l+1)
     return T.sync();
 }
 
-// Neighbour effects of one mover v (moved from l to l+1) on one neighbour w.
-struct InsNbr {
-    int32_t l, snext, par;
-    __device__ __forceinline__ void operator()(const GraphCtx &g, int32_t w, int &cnt_l, bool &push) const {
-        int32_t raw = g.level[w];
-        if (raw & kMoveFlag) return;  // w moved up in this round as well
-        if (raw == l) {
-            cnt_l++;
-        } else if (raw == l + 1) {
-            atomicAdd(&g.up[w], 1);  // v joins Z_{l+1}
-            push = atomicExch(&g.stamp[w], snext) != snext;
-        } else if (raw == l + 2) {
-            atomicAdd(&g.upstar[w], 1);  // v joins Z_{l+1} = Z_{level(w)-1}
-        }
+// Effects of a mover (l -> l+1) on its neighbour w whose level word is raw:
+// a neighbour on l stays below (counted into the mover's up decrement), one on
+// l+1 gains an up-neighbour and becomes a candidate, one on l+2 gains an
+// up*-neighbour.  Returns true if w must be pushed to the next frontier.
+__device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t snext,
+                                           int &cnt_l) {
+    if (w < 0 || (raw & kMoveFlag)) return false;  // empty slot, or w moved up in this round as well
+    if (raw == l) {
+        cnt_l++;
+    } else if (raw == l + 1) {
+        atomicAdd(&g.up[w], 1);
+        return atomicExch(&g.stamp[w], snext) != snext;
+    } else if (raw == l + 2) {
+        atomicAdd(&g.upstar[w], 1);
     }
-};
+    return false;
+}
 
 template <class Team>
-__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) {
+__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0;
+    const int lane = lane_id();
+    const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     for (int r = 0;; ++r) {
         const int p = r & 1, q = p ^ 1;
         // which level does this round process?  (same decision in every thread)
@@ -620,12 +912,23 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
         }
         const int32_t scur = sid_of(g, l), snext = sid_of(g, l + 1);
         const int32_t cut = sh_upmax[l / g.Lg];
+        st.f.gcnt = &g.ctl->fcnt[q];
+        st.f.glist = g.F[q];
+        st.f.gcap = g.n;
+        st.tl.gcnt = &g.ctl->tlcnt[p];
+        st.tl.glist = g.TL[p];
+        st.tl.gcap = g.n;
+        st.cl.gcnt = &g.ctl->clcnt[p];
+        st.cl.glist = g.CL[p];
+        st.cl.gcap = g.clcap;
+        const uint64_t t_round = (g.trace && T.leader()) ? global_ns() : 0;
         // Phase A: candidates on level l = frontier F[p] plus initial candidates at l.
         const int32_t nitems = fc + (s_hi - s_lo);
         for (int i0 = T.wid() * 32; i0 < nitems; i0 += T.nwarps() * 32) {
-            int i = i0 + lane_id();
+            const int i = i0 + lane;
             bool valid = i < nitems, mover = false;
-            int32_t v = 0, upv = 0;
+            int32_t v = 0, upv = 0, c = 0;
+            int64_t off = 0;
             if (valid) {
                 if (i < fc) {
                     v = g.F[p][i];
@@ -638,11 +941,13 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
                 }
             }
             if (valid) {
-                int32_t raw = g.level[v];
+                const int32_t raw = g.level[v];
+                upv = g.up[v];
+                c = g.cap[v];  // fetched with the level: needed if v moves
+                off = g.off[v];
                 if ((raw & kLevelMask) != l) {
                     report(g, kErrInternal, 6, v, raw, l);
                 } else {
-                    upv = g.up[v];
                     mover = upv > cut;  // Invariant 1 violated on level l
                     if (mover) {
                         g.level[v] = (l + 1) | kMoveFlag;
@@ -653,76 +958,100 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
                     }
                 }
             }
-            int fi = warp_append(&g.ctl->fcnt[q], mover);
-            if (mover) g.F[q][fi] = v;
-            enqueue_mover(T, g, p, mover, v, upv);
+            stage_push(st.f, mover, v);
+            enqueue_mover(g, st, mover, v, upv, c, off, wsm);
+        }
+        const uint64_t t_a1 = (g.trace && T.leader()) ? global_ns() : 0;
+        stage_flush_round(g, st, 7u);
+        if (threadIdx.x == 0 && *st.movers) {
+            atomicAdd(&g.ctl->mcnt[p], *st.movers);
+            *st.movers = 0;
         }
         if (!T.sync()) return false;
         // Phase B: scan the movers' neighbours.
+        const uint64_t t_mid = (g.trace && T.leader()) ? global_ns() : 0;
         if (T.leader()) {
-            int32_t mc = g.ctl->mcnt[p];
+            const int32_t mc = g.ctl->mcnt[p];
             if (mc > 0) g.ctl->st[kStRounds] += 1;
             g.ctl->st[kStMoves] += (unsigned long long)mc;
             g.ctl->fcnt[p] = 0;
         }
-        const InsNbr fn{l, snext, p};
-        // thread-mode movers
+        // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
         const int32_t tlc = g.ctl->tlcnt[p];
         for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
-            int i = i0 + lane_id();
-            int4 m = make_int4(0, 0, 0, 0);
-            if (i < tlc) m = g.M[p][g.TL[p][i]];
-            const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + (i < tlc ? g.off[m.x] : 0));
-            int ng = m.z >> 2;
+            const int i = i0 + lane;
+            const int4 it = i < tlc ? g.TL[p][i] : make_int4(0, 0, 0, 0);
+            const int ng = i < tlc ? (1 << it.y) >> 2 : 0;
+            const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
             int cnt_l = 0;
-            int maxg = __reduce_max_sync(kFull, (unsigned)ng);
-            for (int j = 0; j < maxg; ++j) {
-                int4 s4 = j < ng ? t4[j] : make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-                scanned += (j < ng) ? 4 : 0;
-                int32_t ws[4] = {s4.x, s4.y, s4.z, s4.w};
+            for (int j0 = 0; j0 < maxg; j0 += 4) {
+                int32_t ws[16], lv[16];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    bool push = false;
-                    if (ws[k] >= 0) {
-                        visits++;
-                        fn(g, ws[k], cnt_l, push);
-                    }
-                    int fi = warp_append(&g.ctl->fcnt[q], push);
-                    if (push) g.F[q][fi] = ws[k];
+                for (int j = 0; j < 4; ++j) {
+                    const int4 s4 = j0 + j < ng ? pool4[it.z + j0 + j] : empty4();
+                    ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
                 }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+                unsigned push = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    visits += ws[k] >= 0;
+                    if (ins_effect(g, ws[k], lv[k], l, snext, cnt_l)) push |= 1u << k;
+                }
+                scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
+                stage_push_masked(st.f, push, ws);
             }
-            if (i < tlc && cnt_l) atomicSub(&g.up[m.x], cnt_l);
+            if (i < tlc && cnt_l) atomicSub(&g.up[it.x], cnt_l);
         }
-        // warp chunks
+        // chunk items: four per warp iteration, all loads of a step issued together
         const int32_t clc = g.ctl->clcnt[p];
-        for (int c = T.wid(); c < clc; c += T.nwarps()) {
-            int2 it = g.CL[p][c];
-            int4 m = g.M[p][it.x];
-            int j = it.y * (kChunk / 4) + lane_id();
-            bool in = j < (m.z >> 2);
-            int4 s4 = in ? reinterpret_cast<const int4 *>(g.slots + g.off[m.x])[j]
-                         : make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-            scanned += in ? 4 : 0;
-            int cnt_l = 0;
-            int32_t ws[4] = {s4.x, s4.y, s4.z, s4.w};
+        for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
+            int4 it[4];
+            bool in[4];
+            int32_t ws[16], lv[16];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bool push = false;
-                if (ws[k] >= 0) {
-                    visits++;
-                    fn(g, ws[k], cnt_l, push);
-                }
-                int fi = warp_append(&g.ctl->fcnt[q], push);
-                if (push) g.F[q][fi] = ws[k];
+            for (int u = 0; u < 4; ++u) {
+                const int cu = c0 + u * T.nwarps();
+                it[u] = cu < clc ? g.CL[p][cu] : make_int4(0, 0, 0, 0);
+                const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
+                in[u] = cu < clc && j < ((1 << (it[u].y & 31)) >> 2);
+                const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
+                ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
             }
-            cnt_l = warp_sum(cnt_l);
-            if (lane_id() == 0 && cnt_l) atomicSub(&g.up[m.x], cnt_l);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+            int cl4[4] = {0, 0, 0, 0};
+            unsigned push = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                visits += ws[k] >= 0;
+                if (ins_effect(g, ws[k], lv[k], l, snext, cl4[k >> 2])) push |= 1u << k;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
+            stage_push_masked(st.f, push, ws);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int cu = warp_sum(cl4[u]);
+                if (lane == 0 && cu) atomicSub(&g.up[it[u].x], cu);
+            }
         }
+        const uint64_t t_b1 = (g.trace && T.leader()) ? global_ns() : 0;
+        stage_flush_round(g, st, 1u);
         if (!T.sync()) return false;
+        if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
+            int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
+            const uint64_t t_end = global_ns();
+            rec[0] = l; rec[1] = nitems; rec[2] = g.ctl->mcnt[p]; rec[3] = tlc; rec[4] = clc;
+            rec[5] = (int32_t)(t_a1 - t_round); rec[6] = (int32_t)(t_mid - t_a1);
+            rec[7] = (int32_t)(t_b1 - t_mid); rec[8] = (int32_t)(t_end - t_b1);
+            rec[9] = rec[10] = rec[11] = 0;
+        }
     }
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
-    if (lane_id() == 0) {
+    if (lane == 0) {
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
     }
@@ -730,164 +1059,313 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax) 
 }
 
 // ---------------------------------------------------------------------------
-// Steps A5/A6: desire-level and deletion rounds (Algorithms 3 and 4).
+// Step A5: desire-level.
+//
+// dl(w) for w on level lw violating Invariant 2 is the largest x <= lw-2 with
+// cnt(x) >= dnmin[gn(x)], plus one, where cnt(x) is the number of neighbours on
+// levels >= x; 0 if there is none.  The predicate is monotone in x (cnt falls,
+// dnmin[gn(x)] rises), so the group that holds the answer is the highest group
+// whose first level satisfies it (pass 1: per-group counts) and the level inside
+// it comes from a per-level histogram of that group (pass 2, 256-level windows).
+// One warp computes it for a small table, a whole block for a large one.
 // ---------------------------------------------------------------------------
 
-// Desire-level of w (on level lw, violating Invariant 2), computed by one warp:
-// the largest x <= lw-2 with cnt(x) >= dnmin[gn(x)], plus one, where cnt(x) is
-// the number of neighbours on levels >= x; 0 if there is none.  The predicate is
-// monotone in x (cnt falls, dnmin[gn(x)] rises), so the group holding the answer
-// is found from per-group counts (pass 1) and the level inside it from a
-// per-level histogram of that group (pass 2, 256-level windows).
+// Highest group k <= gmax whose first level satisfies the predicate, given the
+// per-group neighbour counts hist[0..G); -1 if none.  One warp.
+__device__ __forceinline__ int warp_best_group(const int32_t *hist, int G, int gmax, const int32_t *sh_dnmin) {
+    const int lane = lane_id();
+    const int per = (G + 31) / 32;  // groups per lane, lane 0 holds the lowest
+    int local = 0;
+    for (int b = 0; b < per; ++b) {
+        const int k = lane * per + b;
+        if (k < G) local += hist[k];
+    }
+    // suffix over lanes: neighbours in groups above this lane's range
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_down_sync(kFull, incl, o);
+        if (lane + o < 32) incl += y;
+    }
+    int run = incl - local;
+    int best = -1;
+    for (int b = per - 1; b >= 0; --b) {
+        const int k = lane * per + b;
+        if (k < G) {
+            run += hist[k];  // run = cnt(k * Lg)
+            if (k <= gmax && run >= sh_dnmin[k] && best < 0) best = k;
+        }
+    }
+    return (int)__reduce_max_sync(kFull, (unsigned)(best + 1)) - 1;
+}
+
+// Largest x in [lo, hi] with above + sum_{y=x..hi} h[y-lo] >= need, or -1.  One warp.
+__device__ __forceinline__ int warp_window_find(const int32_t *h, int lo, int hi, int above, int need) {
+    const int lane = lane_id();
+    const int top = hi - lo;  // lane L covers offsets top-8L .. top-8L-7 (highest levels first)
+    int local = 0;
+    for (int b = 0; b < 8; ++b) {
+        const int idx = top - 8 * lane - b;
+        if (idx >= 0) local += h[idx];
+    }
+    int tot;
+    int run = above + warp_exclusive(local, &tot);
+    int found = -1;
+    for (int b = 0; b < 8; ++b) {
+        const int idx = top - 8 * lane - b;
+        if (idx >= 0 && found < 0) {
+            run += h[idx];
+            if (run >= need) found = lo + idx;
+        }
+    }
+    const unsigned m = __ballot_sync(kFull, found >= 0);
+    return m ? __shfl_sync(kFull, found, __ffs(m) - 1) : -1;
+}
+
 __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
                                      int32_t *hist) {
     if (lw < 2) return 0;
+    const int lane = lane_id();
     const int32_t Lg = g.Lg, G = g.G;
-    const int32_t c = g.cap[w];
+    const int32_t ng = g.cap[w] >> 2;
     const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
     const int32_t xmax = lw - 2;
-    const int32_t gmax = xmax / Lg;  // groups 0..gmax start at or below xmax
-    for (int k = lane_id(); k < G; k += 32) hist[k] = 0;
+    for (int k = lane; k < G; k += 32) hist[k] = 0;
     __syncwarp();
-    for (int j = lane_id(); j < (c >> 2); j += 32) {
-        int4 q = t4[j];
-        if (q.x >= 0) atomicAdd(&hist[g.level[q.x] / Lg], 1);
-        if (q.y >= 0) atomicAdd(&hist[g.level[q.y] / Lg], 1);
-        if (q.z >= 0) atomicAdd(&hist[g.level[q.z] / Lg], 1);
-        if (q.w >= 0) atomicAdd(&hist[g.level[q.w] / Lg], 1);
+    for (int j = lane; j < ng; j += 32) {
+        const int4 q = t4[j];
+        const int32_t a = q.x >= 0 ? g.level[q.x] : -1, b = q.y >= 0 ? g.level[q.y] : -1;
+        const int32_t c = q.z >= 0 ? g.level[q.z] : -1, d = q.w >= 0 ? g.level[q.w] : -1;
+        if (a >= 0) atomicAdd(&hist[a / Lg], 1);
+        if (b >= 0) atomicAdd(&hist[b / Lg], 1);
+        if (c >= 0) atomicAdd(&hist[c / Lg], 1);
+        if (d >= 0) atomicAdd(&hist[d / Lg], 1);
     }
     __syncwarp();
-    // suffix sums: cntg[i] = neighbours on levels >= i*Lg (sequential, G <= 512)
-    if (lane_id() == 0) {
-        int run = 0;
-        for (int k = G - 1; k >= 0; --k) {
-            run += hist[k];
-            hist[k] = run;
-        }
-    }
+    const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
     __syncwarp();
-    int best = -1;
-    for (int k0 = 0; k0 <= gmax; k0 += 32) {
-        int k = k0 + lane_id();
-        bool ok = k <= gmax && hist[k] >= sh_dnmin[k];
-        unsigned m = __ballot_sync(kFull, ok);
-        if (m) best = k0 + 31 - __clz(m);
-    }
     if (best < 0) return 0;
-    const int32_t need = sh_dnmin[best];
-    const int32_t a = best * Lg;
+    const int32_t need = sh_dnmin[best], a = best * Lg;
     int32_t hi = min((best + 1) * Lg - 1, xmax);
-    __syncwarp();
     for (;;) {
         const int32_t lo = max(a, hi - (kWindow - 1));
-        for (int k = lane_id(); k < kWindow + 1; k += 32) hist[k] = 0;
+        for (int k = lane; k < kWindow + 1; k += 32) hist[k] = 0;
         __syncwarp();
-        for (int j = lane_id(); j < (c >> 2); j += 32) {
-            int4 q = t4[j];
-            int32_t ws[4] = {q.x, q.y, q.z, q.w};
+        for (int j = lane; j < ng; j += 32) {
+            const int4 q = t4[j];
+            int32_t lu[4] = {q.x >= 0 ? g.level[q.x] : -1, q.y >= 0 ? g.level[q.y] : -1,
+                             q.z >= 0 ? g.level[q.z] : -1, q.w >= 0 ? g.level[q.w] : -1};
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                if (ws[s] < 0) continue;
-                int32_t lu = g.level[ws[s]];
-                if (lu > hi) atomicAdd(&hist[kWindow], 1);
-                else if (lu >= lo) atomicAdd(&hist[lu - lo], 1);
+                if (lu[s] > hi) atomicAdd(&hist[kWindow], 1);
+                else if (lu[s] >= lo) atomicAdd(&hist[lu[s] - lo], 1);
             }
         }
         __syncwarp();
-        int found = -1;
-        if (lane_id() == 0) {
-            int run = hist[kWindow];
-            for (int x = hi; x >= lo; --x) {
-                run += hist[x - lo];
-                if (run >= need) { found = x; break; }
-            }
-        }
-        found = __shfl_sync(kFull, found, 0);
+        const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
+        __syncwarp();
         if (found >= 0) return found + 1;
         if (lo == a) return a + 1;  // unreachable: cnt(a) >= need holds
         hi = lo - 1;
-        __syncwarp();
     }
 }
 
-// Initial desire-levels: touched vertices that violate Invariant 2 (level > 0 and
-// up* < dnmin[gn(level-1)]) become pending.
-template <class Team>
-__device__ void del_initial(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, int32_t *whist) {
-    const int32_t tc = g.ctl->tcount;
-    unsigned long long evals = 0, evisits = 0;
-    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
-        int i = i0 + lane_id();
-        int32_t x = 0, lx = 0;
-        bool viol = false;
-        if (i < tc) {
-            x = g.touched[i];
-            lx = g.level[x];
-            viol = lx > 0 && g.upstar[x] < sh_dnmin[(lx - 1) / g.Lg];
+// The same computation by the whole block for a large table; hist has
+// max(G, kWindow + 1) ints of block shared memory, *res one int.
+__device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
+                                      int32_t *hist, int32_t *res) {
+    if (lw < 2) return 0;
+    const int32_t Lg = g.Lg, G = g.G;
+    const int32_t ng = g.cap[w] >> 2;
+    const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
+    const int32_t xmax = lw - 2;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+        const int4 q = t4[j];
+        const int32_t a = q.x >= 0 ? g.level[q.x] : -1, b = q.y >= 0 ? g.level[q.y] : -1;
+        const int32_t c = q.z >= 0 ? g.level[q.z] : -1, d = q.w >= 0 ? g.level[q.w] : -1;
+        if (a >= 0) atomicAdd(&hist[a / Lg], 1);
+        if (b >= 0) atomicAdd(&hist[b / Lg], 1);
+        if (c >= 0) atomicAdd(&hist[c / Lg], 1);
+        if (d >= 0) atomicAdd(&hist[d / Lg], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
+        if (threadIdx.x == 0) *res = best;
+    }
+    __syncthreads();
+    const int best = *res;
+    __syncthreads();
+    if (best < 0) return 0;
+    const int32_t need = sh_dnmin[best], a = best * Lg;
+    int32_t hi = min((best + 1) * Lg - 1, xmax);
+    for (;;) {
+        const int32_t lo = max(a, hi - (kWindow - 1));
+        for (int k = threadIdx.x; k < kWindow + 1; k += blockDim.x) hist[k] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+            const int4 q = t4[j];
+            int32_t lu[4] = {q.x >= 0 ? g.level[q.x] : -1, q.y >= 0 ? g.level[q.y] : -1,
+                             q.z >= 0 ? g.level[q.z] : -1, q.w >= 0 ? g.level[q.w] : -1};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (lu[s] > hi) atomicAdd(&hist[kWindow], 1);
+                else if (lu[s] >= lo) atomicAdd(&hist[lu[s] - lo], 1);
+            }
         }
-        unsigned m = __ballot_sync(kFull, viol);
-        while (m) {
-            int src = __ffs(m) - 1;
-            m &= m - 1;
-            int32_t sx = __shfl_sync(kFull, x, src), slx = __shfl_sync(kFull, lx, src);
-            int32_t d = warp_desire_level(g, sx, slx, sh_dnmin, whist);
-            if (lane_id() == 0) {
-                evals++;
-                evisits += g.deg[sx];
-                g.dlv[sx] = d;
-                int pos = atomicAdd(&g.ctl->pcnt[0], 1);
-                g.P[0][pos] = make_int4(sx, d, 0, 0);
-                atomicMin(&g.ctl->nextmin[0], d);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
+            if (threadIdx.x == 0) *res = found;
+        }
+        __syncthreads();
+        const int found = *res;
+        __syncthreads();
+        if (found >= 0) return found + 1;
+        if (lo == a) return a + 1;  // unreachable: cnt(a) >= need holds
+        hi = lo - 1;
+    }
+}
+
+constexpr int32_t kBlockDlCap = 4096;  // tables larger than this get a block per desire-level
+
+// Desire-levels for every vertex of src[0..count) that violates Invariant 2
+// (level > 0 and up* < dnmin[gn(level-1)]).  Two phases with a team barrier:
+// classify into a warp list (small tables, from the front of RL) and a block list
+// (large tables, from the back), then compute.  A result d becomes a pending
+// entry in P[q] unless it equals the vertex's current pending level; results at
+// or below lmin contradict the level lemma and are reported.
+template <class Team>
+__device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t count, int q, int32_t lmin,
+                         const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist, unsigned long long &evals,
+                         unsigned long long &evisits) {
+    const int lane = lane_id();
+    int32_t *RL = g.R[1];
+    for (int i0 = T.wid() * 32; i0 < count; i0 += T.nwarps() * 32) {
+        const int i = i0 + lane;
+        bool viol = false, big = false;
+        int32_t w = 0;
+        if (i < count) {
+            w = src[i];
+            const int32_t lw = g.level[w], us = g.upstar[w], c = g.cap[w];
+            viol = lw > 0 && us < sh_dnmin[(lw - 1) / g.Lg];
+            big = c > kBlockDlCap;
+        }
+        const int pw = warp_append(&g.ctl->rcnt[1], viol && !big);
+        if (viol && !big) RL[pw] = w;
+        const int pb = warp_append(&g.ctl->rbcnt, viol && big);
+        if (viol && big) RL[g.n - 1 - pb] = w;
+    }
+    if (!T.sync()) return false;
+    const int32_t nw = g.ctl->rcnt[1], nb = g.ctl->rbcnt;
+    for (int i = T.wid(); i < nw; i += T.nwarps()) {
+        const int32_t w = RL[i], lw = g.level[w];
+        const int32_t d = warp_desire_level(g, w, lw, sh_dnmin, whist);
+        if (lane == 0) {
+            evals++;
+            evisits += g.deg[w];
+            if (d <= lmin) {
+                report(g, kErrInternal, 8, w, d, lmin);
+            } else if (d != g.dlv[w]) {
+                g.dlv[w] = d;
+                const int pos = atomicAdd(&g.ctl->pcnt[q], 1);
+                g.P[q][pos] = make_int4(w, d, 0, 0);
+                atomicMin(&g.ctl->nextmin[q], d);
             }
         }
     }
-    if (evals) {
-        atomicAdd(&g.ctl->st[kStDlEvals], evals);
-        atomicAdd(&g.ctl->st[kStDlVisits], evisits);
+    for (int i = T.bid(); i < nb; i += (T.nthreads() / blockDim.x)) {
+        const int32_t w = RL[g.n - 1 - i], lw = g.level[w];
+        const int32_t d = block_desire_level(g, w, lw, sh_dnmin, bhist, bhist + kWarpHist);
+        if (threadIdx.x == 0) {
+            evals++;
+            evisits += g.deg[w];
+            if (d <= lmin) {
+                report(g, kErrInternal, 9, w, d, lmin);
+            } else if (d != g.dlv[w]) {
+                g.dlv[w] = d;
+                const int pos = atomicAdd(&g.ctl->pcnt[q], 1);
+                g.P[q][pos] = make_int4(w, d, 0, 0);
+                atomicMin(&g.ctl->nextmin[q], d);
+            }
+        }
     }
+    return true;
 }
 
-// Neighbour effects of one mover v (moved from pv down to l) on neighbour w,
-// plus v's own recount (cu: neighbours >= l, cs: neighbours >= l-1).
-__device__ __forceinline__ void del_nbr(const GraphCtx &g, int32_t w, int32_t l, int32_t pv, int32_t sid, int &cu,
-                                        int &cs, bool &push) {
-    int32_t lw = g.level[w];
+// ---------------------------------------------------------------------------
+// Step A6: deletion rounds (Algorithm 3).
+// ---------------------------------------------------------------------------
+
+// Effects of a mover (pv -> l) on neighbour w with level lw (w did not move if
+// lw > l): v leaves Z_{lw} if lw <= pv and Z_{lw-1} if l < lw-1 <= pv.  The
+// mover's own recount takes cu (neighbours >= l) and cs (>= l-1).  Returns 1 if
+// w must be pushed for a desire-level recheck, 2 if that depends on w being
+// pending (its dlv decides).
+__device__ __forceinline__ int del_effect(const GraphCtx &g, int32_t w, int32_t lw, int32_t l, int32_t pv, int &cu,
+                                          int &cs) {
+    if (w < 0) return 0;
     cu += lw >= l;
     cs += lw >= l - 1;
-    if (lw > l) {  // w did not move this round
-        if (lw <= pv) atomicSub(&g.up[w], 1);                  // v left Z_{level(w)}
-        if (lw - 1 > l && lw - 1 <= pv) atomicSub(&g.upstar[w], 1);  // v left Z_{level(w)-1}
-        if (lw >= l + 2 && (lw - 1 <= pv || g.dlv[w] >= 0)) push = atomicExch(&g.stamp[w], sid) != sid;
-    }
+    if (lw <= l) return 0;
+    if (lw <= pv) atomicSub(&g.up[w], 1);
+    if (lw - 1 > l && lw - 1 <= pv) atomicSub(&g.upstar[w], 1);
+    if (lw < l + 2) return 0;
+    return lw - 1 <= pv ? 1 : 2;
 }
 
 template <class Team>
-__device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, int32_t *whist) {
+__device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist,
+                           int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0, evals = 0, evisits = 0;
+    const int lane = lane_id();
+    const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     for (int r = 0;; ++r) {
         const int p = r & 1, q = p ^ 1;
         const int32_t l = g.ctl->nextmin[p];
         if (l == kInf) break;
         if (r > g.K + 2) {
-            if (T.leader()) report(g, kErrInternal, 7);
+            if (T.leader()) report(g, kErrInternal, 7, l, r, 0);
             return false;
         }
         const int32_t sid = sid_of(g, l);
-        if (T.leader()) g.ctl->rcnt[0] = 0;
+        const uint64_t t_round = (g.trace && T.leader()) ? global_ns() : 0;
+        st.pk.gcnt = &g.ctl->pcnt[q];
+        st.pk.glist = g.P[q];
+        st.pk.gcap = 2 * (int64_t)g.n;
+        st.tl.gcnt = &g.ctl->tlcnt[0];
+        st.tl.glist = g.TL[0];
+        st.tl.gcap = g.n;
+        st.cl.gcnt = &g.ctl->clcnt[0];
+        st.cl.glist = g.CL[0];
+        st.cl.gcap = g.clcap;
+        st.f.gcnt = &g.ctl->rcnt[0];
+        st.f.glist = g.R[0];
+        st.f.gcap = g.n;
+        int32_t kmin = kInf;
+        if (T.leader()) {
+            g.ctl->rcnt[0] = 0;
+            g.ctl->rcnt[1] = 0;
+            g.ctl->rbcnt = 0;
+        }
         // Phase 1: pending entries with dl == l move; the rest stay pending.
         const int32_t pc = g.ctl->pcnt[p];
         for (int i0 = T.wid() * 32; i0 < pc; i0 += T.nwarps() * 32) {
-            int i = i0 + lane_id();
+            const int i = i0 + lane;
             bool mover = false, keep = false;
-            int32_t v = 0, d = 0, pv = 0;
+            int32_t v = 0, d = 0, pv = 0, c = 0;
+            int64_t off = 0;
             if (i < pc) {
-                int4 e = g.P[p][i];
+                const int4 e = g.P[p][i];
                 v = e.x;
                 d = e.y;
                 if (g.dlv[v] == d) {
                     if (d == l) {
                         mover = true;
                         pv = g.level[v];
+                        c = g.cap[v];
+                        off = g.off[v];
                         g.level[v] = l;
                         g.dlv[v] = -1;
                         g.up[v] = 0;
@@ -897,17 +1375,24 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
                     }
                 }
             }
-            int pos = warp_append(&g.ctl->pcnt[q], keep);
-            if (keep) {
-                g.P[q][pos] = make_int4(v, d, 0, 0);
-                atomicMin(&g.ctl->nextmin[q], d);
-            }
-            enqueue_mover(T, g, 0, mover, v, pv);
+            stage_push(st.pk, keep, make_int4(v, d, 0, 0));
+            if (keep) kmin = min(kmin, d);
+            enqueue_mover(g, st, mover, v, pv, c, off, wsm);
+        }
+        kmin = (int32_t)__reduce_min_sync(kFull, (unsigned)kmin);
+        if (lane == 0 && kmin != kInf) atomicMin(st.bmin, kmin);
+        stage_flush_round(g, st, 14u);
+        if (threadIdx.x == 0) {
+            if (*st.movers) atomicAdd(&g.ctl->mcnt[0], *st.movers);
+            if (*st.bmin != kInf) atomicMin(&g.ctl->nextmin[q], *st.bmin);
+            *st.movers = 0;
+            *st.bmin = kInf;
         }
         if (!T.sync()) return false;
         // Phase 2: movers' neighbours.
+        const uint64_t t_mid1 = (g.trace && T.leader()) ? global_ns() : 0;
         if (T.leader()) {
-            int32_t mc = g.ctl->mcnt[0];
+            const int32_t mc = g.ctl->mcnt[0];
             if (mc > 0) g.ctl->st[kStRounds] += 1;
             g.ctl->st[kStMoves] += (unsigned long long)mc;
             g.ctl->pcnt[p] = 0;
@@ -915,104 +1400,111 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
         }
         const int32_t tlc = g.ctl->tlcnt[0];
         for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
-            int i = i0 + lane_id();
-            int4 m = make_int4(0, 0, 0, 0);
-            if (i < tlc) m = g.M[0][g.TL[0][i]];
-            const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + (i < tlc ? g.off[m.x] : 0));
-            int ng = m.z >> 2;
+            const int i = i0 + lane;
+            const int4 it = i < tlc ? g.TL[0][i] : make_int4(0, 0, 0, 0);
+            const int ng = i < tlc ? (1 << it.y) >> 2 : 0;
+            const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
             int cu = 0, cs = 0;
-            int maxg = __reduce_max_sync(kFull, (unsigned)ng);
-            for (int j = 0; j < maxg; ++j) {
-                int4 s4 = j < ng ? t4[j] : make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-                scanned += (j < ng) ? 4 : 0;
-                int32_t ws[4] = {s4.x, s4.y, s4.z, s4.w};
+            for (int j0 = 0; j0 < maxg; j0 += 4) {
+                int32_t ws[16], lv[16];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    bool push = false;
-                    if (ws[k] >= 0) {
-                        visits++;
-                        del_nbr(g, ws[k], l, m.y, sid, cu, cs, push);
-                    }
-                    int ri = warp_append(&g.ctl->rcnt[0], push);
-                    if (push) g.R[0][ri] = ws[k];
+                for (int j = 0; j < 4; ++j) {
+                    const int4 s4 = j0 + j < ng ? pool4[it.z + j0 + j] : empty4();
+                    ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
                 }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+                unsigned push = 0, maybe = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    visits += ws[k] >= 0;
+                    const int e = del_effect(g, ws[k], lv[k], l, it.w, cu, cs);
+                    if (e == 1) push |= 1u << k;
+                    if (e == 2) maybe |= 1u << k;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if ((maybe >> k & 1u) && g.dlv[ws[k]] >= 0) push |= 1u << k;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if ((push >> k & 1u) && atomicExch(&g.stamp[ws[k]], sid) == sid) push &= ~(1u << k);
+                scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
+                stage_push_masked(st.f, push, ws);
             }
             if (i < tlc) {
-                if (cu) atomicAdd(&g.up[m.x], cu);
-                if (cs) atomicAdd(&g.upstar[m.x], cs);
+                if (cu) atomicAdd(&g.up[it.x], cu);
+                if (cs) atomicAdd(&g.upstar[it.x], cs);
             }
         }
         const int32_t clc = g.ctl->clcnt[0];
-        for (int c = T.wid(); c < clc; c += T.nwarps()) {
-            int2 it = g.CL[0][c];
-            int4 m = g.M[0][it.x];
-            int j = it.y * (kChunk / 4) + lane_id();
-            bool in = j < (m.z >> 2);
-            int4 s4 = in ? reinterpret_cast<const int4 *>(g.slots + g.off[m.x])[j]
-                         : make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-            scanned += in ? 4 : 0;
-            int cu = 0, cs = 0;
-            int32_t ws[4] = {s4.x, s4.y, s4.z, s4.w};
+        for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
+            int4 it[4];
+            bool in[4];
+            int32_t ws[16], lv[16];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bool push = false;
-                if (ws[k] >= 0) {
-                    visits++;
-                    del_nbr(g, ws[k], l, m.y, sid, cu, cs, push);
-                }
-                int ri = warp_append(&g.ctl->rcnt[0], push);
-                if (push) g.R[0][ri] = ws[k];
+            for (int u = 0; u < 4; ++u) {
+                const int cu = c0 + u * T.nwarps();
+                it[u] = cu < clc ? g.CL[0][cu] : make_int4(0, 0, 0, 0);
+                const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
+                in[u] = cu < clc && j < ((1 << (it[u].y & 31)) >> 2);
+                const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
+                ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
             }
-            cu = warp_sum(cu);
-            cs = warp_sum(cs);
-            if (lane_id() == 0) {
-                if (cu) atomicAdd(&g.up[m.x], cu);
-                if (cs) atomicAdd(&g.upstar[m.x], cs);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+            int cu4[4] = {0, 0, 0, 0}, cs4[4] = {0, 0, 0, 0};
+            unsigned push = 0, maybe = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                visits += ws[k] >= 0;
+                const int e = del_effect(g, ws[k], lv[k], l, it[k >> 2].w, cu4[k >> 2], cs4[k >> 2]);
+                if (e == 1) push |= 1u << k;
+                if (e == 2) maybe |= 1u << k;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if ((maybe >> k & 1u) && g.dlv[ws[k]] >= 0) push |= 1u << k;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if ((push >> k & 1u) && atomicExch(&g.stamp[ws[k]], sid) == sid) push &= ~(1u << k);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
+            stage_push_masked(st.f, push, ws);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = warp_sum(cu4[u]), b = warp_sum(cs4[u]);
+                if (lane == 0) {
+                    if (a) atomicAdd(&g.up[it[u].x], a);
+                    if (b) atomicAdd(&g.upstar[it[u].x], b);
+                }
             }
         }
+        stage_flush_round(g, st, 1u);
         if (!T.sync()) return false;
         // Phase 3: neighbours that now violate Invariant 2 get their desire-level
         // recomputed (it always lands above l).
+        const uint64_t t_mid2 = (g.trace && T.leader()) ? global_ns() : 0;
+        int32_t tr_movers = 0;
+        if (g.trace && T.leader()) tr_movers = g.ctl->mcnt[0];
         if (T.leader()) {
             g.ctl->mcnt[0] = 0;
             g.ctl->tlcnt[0] = 0;
             g.ctl->clcnt[0] = 0;
         }
-        const int32_t rc = g.ctl->rcnt[0];
-        for (int i0 = T.wid() * 32; i0 < rc; i0 += T.nwarps() * 32) {
-            int i = i0 + lane_id();
-            int32_t w = 0, lw = 0;
-            bool viol = false;
-            if (i < rc) {
-                w = g.R[0][i];
-                lw = g.level[w];
-                viol = g.upstar[w] < sh_dnmin[(lw - 1) / g.Lg];
-            }
-            unsigned m = __ballot_sync(kFull, viol);
-            while (m) {
-                int src = __ffs(m) - 1;
-                m &= m - 1;
-                int32_t sw = __shfl_sync(kFull, w, src), slw = __shfl_sync(kFull, lw, src);
-                int32_t d = warp_desire_level(g, sw, slw, sh_dnmin, whist);
-                if (lane_id() == 0) {
-                    evals++;
-                    evisits += g.deg[sw];
-                    if (d <= l) {
-                        report(g, kErrInternal, 8);
-                    } else if (d != g.dlv[sw]) {
-                        g.dlv[sw] = d;
-                        int pos = atomicAdd(&g.ctl->pcnt[q], 1);
-                        g.P[q][pos] = make_int4(sw, d, 0, 0);
-                        atomicMin(&g.ctl->nextmin[q], d);
-                    }
-                }
-            }
-        }
+        if (!dl_batch(T, g, g.R[0], g.ctl->rcnt[0], q, l, sh_dnmin, whist, bhist, evals, evisits)) return false;
         if (!T.sync()) return false;
+        if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
+            int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
+            const uint64_t t_end = global_ns();
+            rec[0] = l; rec[1] = pc; rec[2] = tr_movers; rec[3] = tlc; rec[4] = clc;
+            rec[5] = (int32_t)(t_mid1 - t_round); rec[6] = (int32_t)(t_mid2 - t_mid1);
+            rec[7] = (int32_t)(t_end - t_mid2);
+            rec[8] = rec[9] = rec[10] = rec[11] = 0;
+        }
     }
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
-    if (lane_id() == 0) {
+    if (lane == 0) {
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
     }
@@ -1024,16 +1516,26 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
 }
 
 // ---------------------------------------------------------------------------
-// One whole batch (Algorithm 1, one half): returns false when the team stopped
-// early (error word set).  sh: shared memory with the group tables, a block-scan
-// scratch and one histogram per warp.
+// One whole batch (Algorithm 1, one half): returns early when the team stopped
+// (error word set).  sh: shared memory with the group tables, a block-scan
+// scratch and one histogram per warp (the first also serves block-wide
+// desire-levels).
 // ---------------------------------------------------------------------------
+// Trace record 0: {kind, then the durations between consecutive marks}.
+__device__ __forceinline__ void trace_steps(const GraphCtx &g, const uint64_t (&t)[8], int n, int32_t kind) {
+    int32_t *rec = g.trace;
+    rec[0] = kind;
+    for (int i = 1; i < 12; ++i) rec[i] = (i < n) ? (int32_t)(t[i] - t[i - 1]) : 0;
+}
+
 template <class Team>
 __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
     int32_t *sh_upmax = sh;
     int32_t *sh_dnmin = sh + kMaxGroups;
-    int *sh_scan = sh + 2 * kMaxGroups;                     // 33 ints
-    int32_t *whist = sh + 2 * kMaxGroups + 64 + (threadIdx.x >> 5) * kWarpHist;
+    int *sh_scan = sh + 2 * kMaxGroups;  // 64 ints
+    int32_t *sh_block = sh + 2 * kMaxGroups + 64;  // kWarpHist + 32 ints, block-wide desire-levels
+    int32_t *whist = sh_block + kWarpHist + 32 + (threadIdx.x >> 5) * kWarpHist;
+    int32_t *sh_stage = sh_block + kWarpHist + 32 + (blockDim.x >> 5) * kWarpHist;
     for (int i = threadIdx.x; i < g.G; i += blockDim.x) {
         sh_upmax[i] = g.upmax[i];
         sh_dnmin[i] = g.dnmin[i];
@@ -1043,11 +1545,21 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
         while (global_ns() - t0 < (uint64_t)g.test_delay_us * 1000u) __nanosleep(1000);
     }
     __syncthreads();
+    // diagnostics: record 0 of the trace holds the durations of the steps before the rounds
+    const bool tr = g.trace && T.leader();
+    uint64_t tmark[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int nmark = 0;
+    if (tr) {
+        g.ctl->trace_n = 1;
+        tmark[nmark++] = global_ns();
+    }
     if (g.B > 0) {
         step_canonicalise(T, g);
         if (!T.sync()) return;  // ids outside [0,n): nothing has changed
+        if (tr) tmark[nmark++] = global_ns();
         step_filter(T, g);
         if (!T.sync()) return;
+        if (tr) tmark[nmark++] = global_ns();
     }
     if (g.op == kOpInsert) {
         step_grow_request(T, g);
@@ -1060,12 +1572,19 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
                 for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
             return;
         }
-        step_grow_apply(T, g);
+        if (tr) tmark[nmark++] = global_ns();
+        if (!step_grow_apply(T, g)) return;
         if (!T.sync()) return;
+        if (tr) tmark[nmark++] = global_ns();
         step_apply_insert(T, g);
         if (!T.sync()) return;
+        if (tr) tmark[nmark++] = global_ns();
         if (!ins_sort_candidates(T, g, sh_scan)) return;
-        ins_rounds(T, g, sh_upmax);
+        if (tr) {
+            tmark[nmark++] = global_ns();
+            trace_steps(g, tmark, nmark, -1);
+        }
+        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage));
     } else {
         if (T.leader()) {
             g.ctl->nextmin[0] = kInf;
@@ -1073,11 +1592,26 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
         }
         step_apply_delete(T, g);
         if (!T.sync()) return;
-        step_shrink(T, g);
+        if (tr) tmark[nmark++] = global_ns();
+        step_shrink(T, g, sh_scan);
         if (!T.sync()) return;
-        del_initial(T, g, sh_dnmin, whist);
+        if (tr) tmark[nmark++] = global_ns();
+        unsigned long long evals = 0, evisits = 0;
+        if (!dl_batch(T, g, g.touched, g.ctl->tcount, 0, -1, sh_dnmin, whist, sh_block, evals, evisits)) return;
+        if (evals) {
+            atomicAdd(&g.ctl->st[kStDlEvals], evals);
+            atomicAdd(&g.ctl->st[kStDlVisits], evisits);
+        }
         if (!T.sync()) return;
-        del_rounds(T, g, sh_dnmin, whist);
+        if (tr) {
+            tmark[nmark++] = global_ns();
+            trace_steps(g, tmark, nmark, -2);
+        }
+        if (T.leader()) {
+            g.ctl->rcnt[1] = 0;
+            g.ctl->rbcnt = 0;
+        }
+        del_rounds(T, g, sh_dnmin, whist, sh_block, whist, stage_setup(sh_stage));
     }
 }
 

@@ -54,7 +54,8 @@ struct Ctl {
     int32_t nextmin[2];   // deletion: smallest pending desire-level
     int32_t err_site;     // which check raised the first error (0 = none)
     int32_t err_info[3];  // values seen by that check (diagnostics)
-    int32_t pad[2];
+    int32_t trace_n;      // per-round records written
+    int32_t rbcnt;        // violators with large tables (block-wide desire-level)
     unsigned long long st[kStCount];
 };
 
@@ -66,6 +67,8 @@ struct GraphCtx {
     int32_t thread_max_cap;
     int32_t load_num, load_den;
     int32_t test_delay_us;
+    int32_t barrier_sleep_ns;
+    int32_t pad1;
     int64_t wait_limit_ns;
     const int32_t *upmax;  // [G]
     const int32_t *dnmin;  // [G]
@@ -92,13 +95,15 @@ struct GraphCtx {
     int32_t *levlist;      // [K] distinct candidate levels
     int32_t *F[2];         // insertion frontier [n]
     int4 *M[2];            // movers {v, aux, cap, -} [n]
-    int32_t *TL[2];        // thread-mode mover indices [n]
-    int2 *CL[2];           // chunk items {mover index, chunk} [clcap]
+    int4 *TL[2];           // thread-mode scan items {v, log2 cap, offset/4, aux} [n]
+    int4 *CL[2];           // chunk scan items {v, chunk<<5 | log2 cap, offset/4, aux} [clcap]
     int64_t clcap;
     int4 *P[2];            // pending {v, dl, -, -} [2n]
-    int32_t *R[2];         // desire-level recompute candidates [n]
+    int32_t *R[2];         // desire-level recompute candidates; R[1]: violators to evaluate [n]
     int32_t *arena;        // table-shrink scratch
     int64_t arena_cap;
+    int32_t *trace;        // per-round diagnostics records (8 int32 each) or null
+    int32_t trace_cap;
     Ctl *ctl;
 };
 

@@ -46,7 +46,7 @@ class PldsTuning(ctypes.Structure):
     _fields_ = [("thread_max_cap", ctypes.c_int32), ("load_num", ctypes.c_int32),
                 ("load_den", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("test_delay_us", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32)]
 
 
 class PldsError(RuntimeError):
@@ -84,6 +84,7 @@ def load():
     L.plds_set_stream.argtypes = [vp, vp]
     L.plds_set_tuning.argtypes = [vp, ctypes.POINTER(PldsTuning)]
     L.plds_set_wait_limit.argtypes = [vp, i64]
+    L.plds_trace.argtypes = [vp, vp, i32]
     L.plds_last_status.argtypes = []
     L.plds_destroy.argtypes = [vp]
     L.plds_destroy.restype = None
@@ -226,6 +227,13 @@ class PLDS:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(load().plds_set_tuning(self._h, ctypes.byref(t)), "plds_set_tuning")
+
+    def trace(self, cap: int = 1 << 16):
+        out = np.zeros((cap, 12), np.int32)
+        k = load().plds_trace(self._h, _ptr(out), cap)
+        if k < 0:
+            raise PldsError(k, "plds_trace")
+        return out[:k]
 
     def set_wait_limit(self, ns: int):
         self._check(load().plds_set_wait_limit(self._h, int(ns)), "plds_set_wait_limit")
