@@ -176,6 +176,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def make_batched(graphs: int, rounds: int, seed: int = 7):
+    """graphs Chung-Lu graphs (n log-uniform in [1e3,1e5], exponent U[2.1,2.8], average
+    degree U[4,32]); half of each graph's edges preloaded (shuffled), then `rounds`
+    mixed batches per graph, each inserting 0.5-5 % of its edges taken from the
+    absent pool and deleting as many present ones (1-10 % of its edges in total);
+    pools are queues, so a deleted edge can come back in a later round."""
+    rng = np.random.default_rng(seed)
+    ns, pre, rnds = [], [], [[] for _ in range(rounds)]
+    for i in range(graphs):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        e = W.chung_lu(n, int(n * rng.uniform(4, 32) / 2), rng.uniform(2.1, 2.8), seed=seed * 100003 + i)
+        e = e[rng.permutation(e.shape[0])]
+        half = e.shape[0] // 2
+        ns.append(n)
+        pre.append(np.ascontiguousarray(e[:half]))
+        present, absent = e[:half], e[half:]
+        for r in range(rounds):
+            k = max(1, int(rng.uniform(0.005, 0.05) * e.shape[0]))
+            k = min(k, present.shape[0], absent.shape[0])
+            ins, dele = absent[:k], present[:k]
+            rnds[r].append((np.ascontiguousarray(ins), np.ascontiguousarray(dele)))
+            absent = np.concatenate([absent[k:], dele])
+            present = np.concatenate([present[k:], ins])
+    return ns, pre, rnds
+
+
+def run_batched(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_03824_gb300 import plds as P
+    torch.cuda.set_device(0)
+    ns, pre, rnds = make_batched(args.graphs, args.rounds)
+    S = P.PLDSSet(ns)
+    e0, o0 = S.pack([(p_, np.zeros((0, 2), np.int32)) for p_ in pre])
+    S.update(torch.from_numpy(e0).cuda(), o0)
+    packed = [S.pack(r) for r in rnds]
+    dev = [(torch.from_numpy(e).cuda(), o) for e, o in packed]
+    upd = [int(o[-1]) for _, o in packed]
+    w = min(args.warmup, args.rounds - 1)
+    for r in range(w):
+        S.update(*dev[r])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(w, args.rounds):
+        S.update(*dev[r])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    lat = dt / (args.rounds - w)
+    batched = sum(upd[w:]) / dt
+    # the plain form: one synchronous insert and delete call per graph, graphs one after another
+    G = [P.PLDS(n) for n in ns]
+    for g, p_ in zip(G, pre):
+        g.insert(torch.from_numpy(p_).cuda())
+    for r in range(w):
+        for g, (ins, dele) in zip(G, rnds[r]):
+            g.insert(torch.from_numpy(ins).cuda())
+            g.delete(torch.from_numpy(dele).cuda())
+    nplain = min(args.rounds - w, args.plain_rounds)
+    devr = [[(torch.from_numpy(i_).cuda(), torch.from_numpy(d_).cuda()) for i_, d_ in rnds[r]]
+            for r in range(w, w + nplain)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for rr in devr:
+        for g, (ins, dele) in zip(G, rr):
+            g.insert(ins)
+            g.delete(dele)
+    torch.cuda.synchronize()
+    dtp = time.perf_counter() - t0
+    plain = sum(upd[w:w + nplain]) / dtp
+    same = all(np.array_equal(a.levels(), b.levels()) for a, b in zip(S.graphs, G)) if nplain == args.rounds - w else None
+    line = {"metric": "edge updates/s, batched form (one launch per round of batches)", "value": batched,
+            "unit": UNIT, "n_gpus": 1, "steps": args.rounds - w, "warmup": w, "ms_per_step": 1e3 * lat,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "form": "batched",
+            "config": {"workload": f"{args.graphs} Chung-Lu graphs, n log-uniform [1e3,1e5], exponent U[2.1,2.8], "
+                                   f"avg degree U[4,32], half preloaded, {args.rounds} mixed rounds of 1-10% of edges",
+                       "total_vertices": int(sum(ns)), "updates_per_round": int(np.mean(upd))},
+            "plain_loop": {"value": plain, "unit": UNIT, "rounds_timed": nplain,
+                           "ms_per_round": 1e3 * dtp / nplain},
+            "speedup_vs_plain": batched / plain, "levels_equal_plain": same}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,9 +272,15 @@ def main():
     ap.add_argument("--cpu-batch", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--graphs", type=int, default=512)
+    ap.add_argument("--rounds", type=int, default=20)
+    ap.add_argument("--plain-rounds", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batched":
+        return run_batched(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -195,6 +195,30 @@ int plds_set_wait_limit(plds_t *h, int64_t ns);
  * returns the number of records written, or a negative PLDS_E* code. */
 int plds_trace(plds_t *h, int32_t *out, int32_t cap);
 
+/*
+ * Batched form: a set of independent graphs updated together, one kernel launch
+ * per round (the paper has no counterpart; it batches many small graphs whose
+ * rounds are too short to fill the GPU one at a time).  Each graph behaves
+ * exactly as a handle of its own: a round applies to graph i its insertion half
+ * and then its deletion half (Algorithm 1), and the resulting state equals that
+ * of plds_batch_insert followed by plds_batch_delete on that graph alone.
+ *   plds_set_create: count graphs with n[i] vertices each (delta, lambda,
+ *     allocator, stream as in plds_create_ex).  NULL on error.
+ *   plds_set_update: edges holds all halves back to back as int32 pairs, host or
+ *     device; offsets has 2*count+1 entries (in edges, not ints): graph i's
+ *     insertion half is pairs [offsets[2i], offsets[2i+1]) and its deletion half
+ *     [offsets[2i+1], offsets[2i+2]).  Blocks until done.  Errors as the single
+ *     calls; an id outside [0, n[i]) rejects the round before graph i changes.
+ *   plds_set_graph: the handle of graph i, owned by the set, for queries and
+ *     statistics (the last round's counts of both halves, summed).
+ */
+typedef struct plds_set plds_set_t;
+plds_set_t *plds_set_create(int32_t count, const int32_t *n, double delta, double lambda,
+                            const plds_allocator *allocator, void *stream);
+int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_t *offsets);
+plds_t *plds_set_graph(plds_set_t *s, int32_t i);
+void plds_set_destroy(plds_set_t *s);
+
 /* Status code of the calling thread's last call. */
 int plds_last_status(void);
 

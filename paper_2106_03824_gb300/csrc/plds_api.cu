@@ -33,7 +33,7 @@ static int set_status(int s) {
 __global__ void __launch_bounds__(512) k_batch_grid(const __grid_constant__ GraphCtx g) {
     extern __shared__ int32_t sh[];
     GridTeam T{g.ctl, g.wait_limit_ns, g.barrier_sleep_ns};
-    run_batch(T, g, sh);
+    run_batch(T, g, sh, 0);
 }
 
 // Coreness estimate (Definition "Coreness Estimate"): exponent
@@ -249,8 +249,11 @@ static bool ensure_batch_scratch(plds *h, int64_t B) {
 
 static int block_threads(const plds *h) { return h->tune.block_threads > 0 ? h->tune.block_threads : 512; }
 
-static size_t smem_bytes(int threads) {
-    return sizeof(int32_t) * (size_t)(2 * kMaxGroups + 64 + kWarpHist + 32 + (threads / 32) * kWarpHist + kStageInts);
+// Dynamic shared memory of a batch kernel block: group tables, scan scratch,
+// block-wide desire-level histogram, one histogram per warp, staging area.
+static size_t smem_bytes(int threads, int stage_shift = 0) {
+    return sizeof(int32_t) *
+           (size_t)(2 * kMaxGroups + 64 + kWarpHist + 32 + (threads / 32) * kWarpHist + stage_ints(stage_shift));
 }
 
 // Move every table into a new pool laid out back to back, with room for `extra`
@@ -843,4 +846,291 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
     return set_status(PLDS_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent graphs, one launch per round of batches.
+//
+// A set owns `count` ordinary handles.  One round applies one mixed batch to
+// every graph (its insertion half, then its deletion half, as Algorithm 1
+// orders them).  The kernel is persistent: each block takes the next graph from
+// a work counter (graphs ordered by decreasing size) and runs that graph's whole
+// round with the same device routines as the single-graph kernel, the block
+// being the team (block barriers only, graphs progress independently).  The
+// per-round launch sequence (descriptor upload, counter reset, kernel, control
+// word read-back) is captured once in a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+namespace {
+struct SetItem {
+    GraphCtx half[2];  // 0: insertion half, 1: deletion half
+};
+constexpr int kSetThreads = 256;
+constexpr int kSetStageShift = 3;
+}  // namespace
+
+__global__ void __launch_bounds__(kSetThreads, 2)
+    k_batch_set(const SetItem *__restrict__ items, int32_t count, int32_t *next) {
+    extern __shared__ int32_t sh[];
+    __shared__ GraphCtx gsh;
+    __shared__ int32_t idx;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) idx = atomicAdd(next, 1);
+        __syncthreads();
+        const int i = idx;
+        if (i >= count) return;
+        for (int h = 0; h < 2; ++h) {
+            __syncthreads();
+            const int32_t *src = reinterpret_cast<const int32_t *>(&items[i].half[h]);
+            int32_t *dst = reinterpret_cast<int32_t *>(&gsh);
+            for (int k = threadIdx.x; k < (int)(sizeof(GraphCtx) / 4); k += blockDim.x) dst[k] = src[k];
+            __syncthreads();
+            if (gsh.B == 0) continue;  // an empty half changes nothing
+            int32_t *cw = reinterpret_cast<int32_t *>(gsh.ctl);
+            for (int k = threadIdx.x; k < (int)(sizeof(Ctl) / 4); k += blockDim.x) cw[k] = 0;
+            for (int64_t k = threadIdx.x; k < gsh.hcap; k += blockDim.x) gsh.hset[k] = kEmptyKey;
+            if (gsh.op == kOpInsert)
+                for (int k = threadIdx.x; k <= gsh.K; k += blockDim.x) gsh.bins[k] = 0;
+            __syncthreads();
+            BlockTeam T{gsh.ctl};
+            run_batch(T, gsh, sh, kSetStageShift);
+            __syncthreads();
+            if (ld_volatile(&gsh.ctl->err) != 0) break;  // the host resolves it and reruns this graph
+        }
+    }
+}
+
+struct plds_set {
+    int32_t count = 0;
+    std::vector<plds *> g;       // graph handles
+    std::vector<int32_t> order;  // graphs by decreasing n
+    cudaStream_t stream = nullptr;   // the caller's stream (allocations, copies)
+    cudaStream_t run = nullptr;      // private stream the captured round is replayed on
+    bool graph_ok = true;
+    plds *owner = nullptr;       // allocator and device of the set's own buffers
+    DevBuf items, ctls, next, edges;
+    int64_t edges_cap = 0;
+    SetItem *h_items = nullptr;  // pinned
+    Ctl *h_ctls = nullptr;       // pinned
+    int grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t captured_count = -1;
+};
+
+// Runs one round for n_items graphs on the private stream (the caller's stream
+// has been synchronised, so everything it enqueued before is visible).
+static int set_launch(plds_set *s, int32_t n_items, bool use_graph) {
+    const size_t smem = smem_bytes(kSetThreads, kSetStageShift);
+    cudaStream_t st = s->run;
+    use_graph = use_graph && s->graph_ok;
+    if (use_graph && s->exec && s->captured_count == n_items) return cudaGraphLaunch(s->exec, st) == cudaSuccess ? 0 : -1;
+    auto enqueue = [&]() {
+        cudaMemcpyAsync(s->items.p, s->h_items, sizeof(SetItem) * (size_t)n_items, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(s->next.p, 0, sizeof(int32_t), st);
+        k_batch_set<<<s->grid, kSetThreads, smem, st>>>(P<SetItem>(s->items), n_items, P<int32_t>(s->next));
+        cudaMemcpyAsync(s->h_ctls, s->ctls.p, sizeof(Ctl) * 2 * (size_t)n_items, cudaMemcpyDeviceToHost, st);
+    };
+    if (!use_graph) {
+        enqueue();
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    if (s->exec) {
+        cudaGraphExecDestroy(s->exec);
+        s->exec = nullptr;
+    }
+    if (s->graph) {
+        cudaGraphDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        enqueue();
+        ok = cudaStreamEndCapture(st, &s->graph) == cudaSuccess &&
+             cudaGraphInstantiate(&s->exec, s->graph, 0) == cudaSuccess;
+    }
+    if (!ok) {  // capture unavailable: launch directly from now on
+        cudaGetLastError();
+        s->graph_ok = false;
+        enqueue();
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    s->captured_count = n_items;
+    return cudaGraphLaunch(s->exec, st) == cudaSuccess ? 0 : -1;
+}
+
+extern "C" plds_set_t *plds_set_create(int32_t count, const int32_t *n, double delta, double lambda,
+                                       const plds_allocator *allocator, void *stream) {
+    if (count <= 0 || !n) {
+        set_status(PLDS_EINVAL);
+        return nullptr;
+    }
+    plds_set *s = new (std::nothrow) plds_set();
+    if (!s) {
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    s->count = count;
+    s->stream = (cudaStream_t)stream;
+    for (int32_t i = 0; i < count; ++i) {
+        plds_t *h = plds_create_ex(n[i], delta, lambda, 0, allocator, stream, 0);
+        if (!h) {
+            int rc = plds_last_status();
+            plds_set_destroy(s);
+            set_status(rc);
+            return nullptr;
+        }
+        s->g.push_back(h);
+    }
+    s->owner = s->g[0];
+    if (cudaStreamCreateWithFlags(&s->run, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        plds_set_destroy(s);
+        set_status(PLDS_EDEVICE);
+        return nullptr;
+    }
+    s->order.resize(count);
+    for (int32_t i = 0; i < count; ++i) s->order[i] = i;
+    std::stable_sort(s->order.begin(), s->order.end(), [&](int a, int b) { return s->g[a]->n > s->g[b]->n; });
+    if (!dev_get(s->owner, s->items, sizeof(SetItem) * (size_t)count) ||
+        !dev_get(s->owner, s->ctls, sizeof(Ctl) * 2 * (size_t)count) || !dev_get(s->owner, s->next, 16) ||
+        cudaMallocHost(&s->h_items, sizeof(SetItem) * (size_t)count) != cudaSuccess ||
+        cudaMallocHost(&s->h_ctls, sizeof(Ctl) * 2 * (size_t)count) != cudaSuccess) {
+        cudaGetLastError();
+        plds_set_destroy(s);
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    const size_t smem = smem_bytes(kSetThreads, kSetStageShift);
+    cudaFuncSetAttribute(k_batch_set, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_set, kSetThreads, smem);
+    s->grid = std::max(1, occ) * s->owner->num_sms;
+    set_status(PLDS_OK);
+    return s;
+}
+
+extern "C" plds_t *plds_set_graph(plds_set_t *s, int32_t i) {
+    if (!s || i < 0 || i >= s->count) {
+        set_status(PLDS_EINVAL);
+        return nullptr;
+    }
+    set_status(PLDS_OK);
+    return s->g[i];
+}
+
+extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_t *offsets) {
+    if (!s || !offsets) return set_status(PLDS_EINVAL);
+    const int32_t G = s->count;
+    const int64_t total = offsets[2 * G];
+    if (offsets[0] != 0 || total < 0 || (total > 0 && !edges)) return set_status(PLDS_EINVAL);
+    for (int32_t k = 0; k < 2 * G; ++k)
+        if (offsets[k + 1] < offsets[k]) return set_status(PLDS_EINVAL);
+    for (plds *h : s->g)
+        if (h->poisoned) return set_status(PLDS_EPOISONED);
+    plds *o = s->owner;
+    cudaSetDevice(o->device);
+    const int32_t *dedges = edges;
+    if (total > 0 && !is_device_ptr(edges)) {
+        if (total > s->edges_cap) {
+            if (!dev_get(o, s->edges, sizeof(int32_t) * 2 * (size_t)total)) return set_status(PLDS_ENOMEM);
+            s->edges_cap = total;
+        }
+        cudaMemcpyAsync(s->edges.p, edges, sizeof(int32_t) * 2 * (size_t)total, cudaMemcpyHostToDevice, s->stream);
+        dedges = P<int32_t>(s->edges);
+    }
+    // graphs still to run this round (all at first; then the ones that needed a bigger pool)
+    std::vector<int32_t> todo(s->order);
+    Ctl *dctl = P<Ctl>(s->ctls);
+    for (int attempt = 0; attempt < 4 && !todo.empty(); ++attempt) {
+        const int32_t m = (int32_t)todo.size();
+        for (int32_t j = 0; j < m; ++j) {
+            const int32_t gi = todo[j];
+            plds *h = s->g[gi];
+            const int64_t bi = offsets[2 * gi + 1] - offsets[2 * gi], bd = offsets[2 * gi + 2] - offsets[2 * gi + 1];
+            if (!ensure_batch_scratch(h, std::max<int64_t>(std::max(bi, bd), 1))) return set_status(PLDS_ENOMEM);
+            std::memset(&h->last, 0, sizeof(h->last));
+            h->last.submitted = bi + bd;
+            for (int half = 0; half < 2; ++half) {
+                const int64_t b = half == 0 ? bi : bd;
+                if ((int64_t)h->stamp_base + 2 * (int64_t)h->T.K + 8 >= 0x7fffffff) {
+                    cudaMemsetAsync(h->stamp.p, 0, sizeof(int32_t) * (size_t)h->n, s->stream);
+                    h->stamp_base = 1;
+                }
+                GraphCtx g = make_ctx(h, half == 0 ? kOpInsert : kOpDelete, dedges + 2 * offsets[2 * gi + half], b);
+                g.thread_max_cap = std::min(g.thread_max_cap, 16);
+                g.ctl = dctl + 2 * j + half;
+                g.trace = nullptr;
+                g.trace_cap = 0;
+                s->h_items[j].half[half] = g;
+                if (b > 0) h->stamp_base += h->T.K + 2;
+            }
+        }
+        // the first pass over all graphs replays the captured round; reruns launch directly
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess || set_launch(s, m, attempt == 0) != 0 ||
+            cudaStreamSynchronize(s->run) != cudaSuccess) {
+            cudaGetLastError();
+            for (plds *h : s->g) h->poisoned = true;
+            return set_status(PLDS_EDEVICE);
+        }
+        o->launches += 1;
+        std::vector<int32_t> again;
+        for (int32_t j = 0; j < m; ++j) {
+            const int32_t gi = todo[j];
+            plds *h = s->g[gi];
+            const Ctl &ci = s->h_ctls[2 * j], &cd = s->h_ctls[2 * j + 1];
+            const int32_t err = ci.err | cd.err;
+            if (err & kErrInvalidId) return set_status(PLDS_EINVAL);
+            if (err == kErrNeedPool) {
+                int rc = grow_pool(h, (int64_t)ci.grow_total);
+                if (rc) return set_status(rc);
+                again.push_back(gi);
+                continue;
+            }
+            if (err) {
+                h->poisoned = true;
+                h->last.err_bits = err;
+                h->last.err_site = ci.err ? ci.err_site : cd.err_site;
+                return set_status(PLDS_EINTERNAL);
+            }
+            for (const Ctl *c : {&ci, &cd}) {
+                h->last.self_loops += (int64_t)c->st[kStSelfLoops];
+                h->last.filtered += (int64_t)c->st[kStFiltered];
+                h->last.valid += (int64_t)c->vcount;
+                h->last.rounds += (int64_t)c->st[kStRounds];
+                h->last.moves += (int64_t)c->st[kStMoves];
+                h->last.visits += (int64_t)c->st[kStVisits];
+                h->last.dl_evals += (int64_t)c->st[kStDlEvals];
+                h->last.dl_visits += (int64_t)c->st[kStDlVisits];
+                h->last.slots_scanned += (int64_t)c->st[kStSlotsScanned];
+            }
+            const int64_t bi = offsets[2 * gi + 1] - offsets[2 * gi], bd = offsets[2 * gi + 2] - offsets[2 * gi + 1];
+            h->last.duplicates = (bi > 0 ? bi - (int64_t)ci.st[kStSelfLoops] - (int64_t)ci.ucount : 0) +
+                                 (bd > 0 ? bd - (int64_t)cd.st[kStSelfLoops] - (int64_t)cd.ucount : 0);
+        }
+        todo.swap(again);
+    }
+    return set_status(todo.empty() ? PLDS_OK : PLDS_ENOMEM);
+}
+
+extern "C" void plds_set_destroy(plds_set_t *s) {
+    if (!s) return;
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->run) {
+        cudaStreamSynchronize(s->run);
+        cudaStreamDestroy(s->run);
+    }
+    if (s->owner) {
+        dev_free(s->owner, s->items);
+        dev_free(s->owner, s->ctls);
+        dev_free(s->owner, s->next);
+        dev_free(s->owner, s->edges);
+        cudaStreamSynchronize(s->stream);
+    }
+    if (s->h_items) cudaFreeHost(s->h_items);
+    if (s->h_ctls) cudaFreeHost(s->h_ctls);
+    for (plds *h : s->g) plds_destroy(h);
+    cudaGetLastError();
+    delete s;
 }

@@ -678,8 +678,6 @@ __device__ __forceinline__ void stage_flush(const GraphCtx &g, const Stage<V> &s
 }
 
 constexpr int kStageF = 2048, kStageTL = 1024, kStageCL = 2048, kStagePK = 1024;
-// shared ints used by the staging area
-constexpr int kStageInts = 16 + kStageF + 4 * (kStageTL + kStageCL + kStagePK);
 
 // Shared-memory staging of one round: frontier / recompute list, thread-mode and
 // chunk scan items, pending entries, and the block's mover count.
@@ -691,30 +689,37 @@ struct RoundStage {
     int32_t *tmp;
 };
 
-// Lay out the staging area (kStageInts ints of shared memory, 16-byte aligned).
-__device__ __forceinline__ RoundStage stage_setup(int32_t *base) {
+// Shared ints of a staging area whose capacities are the defaults >> shift
+// (a block-sized team, alone on its graph, needs far less room than a grid).
+__host__ __device__ constexpr int stage_ints(int shift) {
+    return 16 + (kStageF >> shift) + 4 * ((kStageTL >> shift) + (kStageCL >> shift) + (kStagePK >> shift));
+}
+
+// Lay out the staging area (stage_ints(shift) ints of shared memory, 16-byte aligned).
+__device__ __forceinline__ RoundStage stage_setup(int32_t *base, int shift) {
     RoundStage st{};
+    const int cf = kStageF >> shift, ct = kStageTL >> shift, cc = kStageCL >> shift, cp = kStagePK >> shift;
     int32_t *hdr = base;
     st.f.buf = base + 16;
-    st.tl.buf = reinterpret_cast<int4 *>(base + 16 + kStageF);
-    st.cl.buf = st.tl.buf + kStageTL;
-    st.pk.buf = st.cl.buf + kStageCL;
+    st.tl.buf = reinterpret_cast<int4 *>(base + 16 + cf);
+    st.cl.buf = st.tl.buf + ct;
+    st.pk.buf = st.cl.buf + cc;
     st.f.hdr = hdr;
     st.tl.hdr = hdr + 2;
     st.cl.hdr = hdr + 4;
     st.pk.hdr = hdr + 6;
-    st.f.cap = kStageF;
-    st.tl.cap = kStageTL;
-    st.cl.cap = kStageCL;
-    st.pk.cap = kStagePK;
+    st.f.cap = cf;
+    st.tl.cap = ct;
+    st.cl.cap = cc;
+    st.pk.cap = cp;
     st.movers = hdr + 8;
     st.bmin = hdr + 9;
     st.tmp = hdr + 10;  // 4 ints
     if (threadIdx.x == 0) {
-        hdr[0] = 0; hdr[1] = kStageF;
-        hdr[2] = 0; hdr[3] = kStageTL;
-        hdr[4] = 0; hdr[5] = kStageCL;
-        hdr[6] = 0; hdr[7] = kStagePK;
+        hdr[0] = 0; hdr[1] = cf;
+        hdr[2] = 0; hdr[3] = ct;
+        hdr[4] = 0; hdr[5] = cc;
+        hdr[6] = 0; hdr[7] = cp;
         hdr[8] = 0; hdr[9] = kInf;
     }
     __syncthreads();
@@ -1529,7 +1534,7 @@ __device__ __forceinline__ void trace_steps(const GraphCtx &g, const uint64_t (&
 }
 
 template <class Team>
-__device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
+__device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh, int stage_shift) {
     int32_t *sh_upmax = sh;
     int32_t *sh_dnmin = sh + kMaxGroups;
     int *sh_scan = sh + 2 * kMaxGroups;  // 64 ints
@@ -1584,7 +1589,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
             tmark[nmark++] = global_ns();
             trace_steps(g, tmark, nmark, -1);
         }
-        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage));
+        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
     } else {
         if (T.leader()) {
             g.ctl->nextmin[0] = kInf;
@@ -1611,7 +1616,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh) {
             g.ctl->rcnt[1] = 0;
             g.ctl->rbcnt = 0;
         }
-        del_rounds(T, g, sh_dnmin, whist, sh_block, whist, stage_setup(sh_stage));
+        del_rounds(T, g, sh_dnmin, whist, sh_block, whist, stage_setup(sh_stage, stage_shift));
     }
 }
 

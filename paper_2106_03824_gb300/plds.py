@@ -85,6 +85,13 @@ def load():
     L.plds_set_tuning.argtypes = [vp, ctypes.POINTER(PldsTuning)]
     L.plds_set_wait_limit.argtypes = [vp, i64]
     L.plds_trace.argtypes = [vp, vp, i32]
+    L.plds_set_create.restype = vp
+    L.plds_set_create.argtypes = [i32, vp, dbl, dbl, ctypes.POINTER(PldsAllocator), vp]
+    L.plds_set_update.argtypes = [vp, vp, vp]
+    L.plds_set_graph.restype = vp
+    L.plds_set_graph.argtypes = [vp, i32]
+    L.plds_set_destroy.argtypes = [vp]
+    L.plds_set_destroy.restype = None
     L.plds_last_status.argtypes = []
     L.plds_destroy.argtypes = [vp]
     L.plds_destroy.restype = None
@@ -132,13 +139,18 @@ class PLDS:
     """One graph on the current CUDA device; wraps a plds_t handle."""
 
     def __init__(self, n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0,
-                 torch_allocator: bool = True, stream=None):
+                 torch_allocator: bool = True, stream=None, _borrowed=None):
         L = load()
         self.n = int(n)
-        self._alloc = _torch_allocator() if torch_allocator else None
-        st = stream if stream is not None else (_torch_stream() if torch_allocator else None)
-        self._h = L.plds_create_ex(self.n, float(delta), float(lam), int(levels_per_group),
-                                   ctypes.byref(self._alloc) if self._alloc else None, st, 0)
+        self._owned = _borrowed is None
+        if _borrowed is not None:  # a graph owned by a PLDSSet
+            self._alloc = None
+            self._h = _borrowed
+        else:
+            self._alloc = _torch_allocator() if torch_allocator else None
+            st = stream if stream is not None else (_torch_stream() if torch_allocator else None)
+            self._h = L.plds_create_ex(self.n, float(delta), float(lam), int(levels_per_group),
+                                       ctypes.byref(self._alloc) if self._alloc else None, st, 0)
         if not self._h:
             raise PldsError(L.plds_last_status(), "plds_create_ex")
         p = np.zeros(4, np.int32)
@@ -151,7 +163,8 @@ class PLDS:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().plds_destroy(self._h)
+            if self._owned:
+                load().plds_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -240,6 +253,58 @@ class PLDS:
 
     def set_stream(self, stream):
         self._check(load().plds_set_stream(self._h, stream), "plds_set_stream")
+
+
+class PLDSSet:
+    """Independent graphs updated together, one kernel launch per round (batched form)."""
+
+    def __init__(self, ns, delta: float = 0.4, lam: float = 3.0, torch_allocator: bool = True):
+        L = load()
+        self.ns = [int(x) for x in ns]
+        arr = np.asarray(self.ns, np.int32)
+        self._alloc = _torch_allocator() if torch_allocator else None
+        st = _torch_stream() if torch_allocator else None
+        self._s = L.plds_set_create(len(self.ns), _ptr(arr), float(delta), float(lam),
+                                    ctypes.byref(self._alloc) if self._alloc else None, st)
+        if not self._s:
+            raise PldsError(L.plds_last_status(), "plds_set_create")
+        self.graphs = [PLDS(n, _borrowed=L.plds_set_graph(self._s, i)) for i, n in enumerate(self.ns)]
+
+    def update(self, edges, offsets, check=True) -> int:
+        """edges: int32 [total,2] (host array or cuda tensor); offsets: int64 [2*count+1]."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if isinstance(edges, np.ndarray):
+            edges = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        rc = load().plds_set_update(self._s, _ptr(edges), _ptr(off))
+        if check and rc != PLDS_OK:
+            raise PldsError(rc, "plds_set_update")
+        return rc
+
+    @staticmethod
+    def pack(halves):
+        """[(ins_i, del_i)] per graph -> (edges [total,2], offsets [2*count+1])."""
+        parts, offs, pos = [], [0], 0
+        for ins, dele in halves:
+            for h in (ins, dele):
+                h = np.asarray(h, np.int32).reshape(-1, 2)
+                parts.append(h)
+                pos += h.shape[0]
+                offs.append(pos)
+        edges = np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros((0, 2), np.int32)
+        return edges, np.asarray(offs, np.int64)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            for g in self.graphs:
+                g._h = None
+            load().plds_set_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exported_symbols_in_header(header: os.PathLike | None = None):

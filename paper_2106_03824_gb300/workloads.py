@@ -21,6 +21,17 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
+def _sorted_unique(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent compare)."""
+    k = np.sort(keys, kind="stable")
+    if k.size == 0:
+        return k
+    keep = np.empty(k.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(k[1:], k[:-1], out=keep[1:])
+    return k[keep]
+
+
 def _canonical_unique(u: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Drop self-loops, orient u<v, drop duplicates; returns int32[m,2] sorted by key."""
     u = u.astype(np.int64, copy=False)
@@ -29,7 +40,7 @@ def _canonical_unique(u: np.ndarray, v: np.ndarray) -> np.ndarray:
     u, v = u[keep], v[keep]
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
-    key = np.unique((lo << 32) | hi)
+    key = _sorted_unique((lo << 32) | hi)
     out = np.empty((key.size, 2), dtype=np.int32)
     out[:, 0] = (key >> 32).astype(np.int32)
     out[:, 1] = (key & 0xFFFFFFFF).astype(np.int32)
@@ -65,14 +76,16 @@ def chung_lu(n: int, m: int, gamma: float, seed: int = 1) -> np.ndarray:
     keys = np.zeros(0, dtype=np.int64)
     drawn = 0
     while keys.size < m and drawn < 4 * m:
-        k = min(max(m - keys.size, 1024) * 2, 4 * m - drawn)
+        # draw enough for the remaining edges at the duplicate rate seen so far
+        rate = drawn / max(keys.size, 1) if drawn else 1.2
+        k = int(min(max((m - keys.size) * rate * 1.25, 4096), 4 * m - drawn))
         u = np.searchsorted(cdf, rng.random(k), side="right").clip(0, n - 1)
         v = np.searchsorted(cdf, rng.random(k), side="right").clip(0, n - 1)
         drawn += k
         keep = u != v
         lo = np.minimum(u[keep], v[keep]).astype(np.int64)
         hi = np.maximum(u[keep], v[keep]).astype(np.int64)
-        keys = np.unique(np.concatenate([keys, (lo << 32) | hi]))
+        keys = _sorted_unique(np.concatenate([keys, (lo << 32) | hi]))
     if keys.size > m:
         keys = rng.permutation(keys)[:m]
     e = np.empty((keys.size, 2), dtype=np.int32)
