@@ -219,6 +219,46 @@ int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_t *offsets)
 plds_t *plds_set_graph(plds_set_t *s, int32_t i);
 void plds_set_destroy(plds_set_t *s);
 
+/*
+ * Serving form: a device-resident request loop over one graph (the paper has no
+ * counterpart).  One persistent kernel applies requests from a ring of `slots`
+ * slots in pinned host memory, strictly in submission order and with unchanged
+ * batch boundaries, so the graph ends exactly as if each request had been its own
+ * plds_batch_insert / plds_batch_delete call; coreness queries in between see the
+ * state after every earlier request.  While a server is open on a handle, use
+ * only the server calls on that handle.
+ *   plds_server_create: slots in the ring; max_batch = largest batch (edges).
+ *   plds_server_submit: op 0 insertion batch, 1 deletion batch, 2 coreness query
+ *     (out = double[n], host or device; edges ignored).  Edge arrays may be device
+ *     memory or pinned host memory (read in place by the running loop: their
+ *     contents must be complete at submission -- no copy still in flight on a
+ *     stream -- and unchanged until the request has finished) or pageable host
+ *     memory (copied at submission).  Blocks
+ *     only while every slot is busy.  *ticket gets the request's number (0, 1, ...).
+ *   plds_server_poll: copies up to cap finished requests into out (oldest first);
+ *     returns their count or a negative code.
+ *   plds_server_drain: waits until every submitted request has finished.
+ *   plds_server_destroy: drains, stops the loop, frees the server (not the graph).
+ * Pool growth is gated by free device memory (1 GiB kept free); a request that
+ * cannot get room finishes with PLDS_ENOMEM reported by the call that noticed it.
+ */
+typedef struct plds_server plds_server_t;
+typedef struct plds_request_result {
+    int64_t ticket;
+    int32_t op;
+    int32_t status;     /* PLDS_OK or a PLDS_E* code */
+    int64_t valid;      /* updates applied */
+    int64_t rounds;
+    int64_t moves;
+    int64_t device_ns;  /* time the device spent on the request */
+} plds_request_result;
+plds_server_t *plds_server_create(plds_t *h, int32_t slots, int64_t max_batch);
+int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *edges, int64_t B, double *out,
+                       int64_t *ticket);
+int plds_server_poll(plds_server_t *sv, plds_request_result *out, int32_t cap);
+int plds_server_drain(plds_server_t *sv);
+void plds_server_destroy(plds_server_t *sv);
+
 /* Status code of the calling thread's last call. */
 int plds_last_status(void);
 

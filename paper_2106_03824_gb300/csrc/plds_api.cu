@@ -8,9 +8,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <vector>
 
@@ -280,6 +284,20 @@ static int grow_pool(plds *h, int64_t extra) {
     if (rc) return rc;
     int64_t want = std::max<int64_t>(h->pool_cap, 2 * (live + extra));
     want = (want + 3) & ~(int64_t)3;
+    // gate on free HBM: keep 1 GiB free for everything else on the device
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+        (int64_t)free_b - (int64_t)(1ll << 30) < 4 * want) {
+        const int64_t fit = ((int64_t)free_b - (int64_t)(1ll << 30)) / 4;
+        want = std::max<int64_t>(live + extra + 4, fit) & ~(int64_t)3;
+        if (want < live + extra) {
+            dev_free(h, bsum);
+            dev_free(h, newoff);
+            dev_free(h, total);
+            return PLDS_ENOMEM;
+        }
+    }
+    cudaGetLastError();
     if (want / 4 >= ((int64_t)1 << 31)) {  // scan items address the pool in int32 units of 4 slots
         dev_free(h, bsum);
         dev_free(h, newoff);
@@ -1133,4 +1151,445 @@ extern "C" void plds_set_destroy(plds_set_t *s) {
     for (plds *h : s->g) plds_destroy(h);
     cudaGetLastError();
     delete s;
+}
+
+// ---------------------------------------------------------------------------
+// Serving form: a device-resident request loop.
+//
+// One persistent cooperative kernel serves a graph.  Requests (an insertion
+// batch, a deletion batch, or a coreness query) sit in a ring of slots in
+// pinned host memory that the device reads directly; the kernel's leader thread
+// polls the next slot, the grid applies the request with the same routines as a
+// single batch call, and the leader writes the completion record back into the
+// slot.  Requests are applied strictly in submission order with unchanged
+// boundaries, so the graph ends up exactly as if each request had been a
+// separate call.  The host admits a new request whenever a slot is free: its
+// copy-in overlaps with the device working on earlier requests, and no kernel
+// launch or host synchronisation sits between requests.  The loop exits after
+// an idle period or when the adjacency pool needs to grow (the host grows it,
+// gated by free HBM, and relaunches).
+// ---------------------------------------------------------------------------
+namespace {
+enum : int32_t { kSlotFree = 0, kSlotReady = 1, kSlotDone = 2 };
+enum : int32_t { kReqInsert = 0, kReqDelete = 1, kReqCoreness = 2 };
+enum : int32_t { kExitNone = 0, kExitIdle = 1, kExitNeedPool = 2, kExitError = 3 };
+
+struct alignas(64) ReqSlot {
+    int32_t state;  // kSlot*
+    int32_t op;     // kReq*
+    int64_t B;
+    const int32_t *edges;  // device-accessible
+    double *out;           // device-accessible (coreness queries)
+    int64_t ticket;
+    // written by the device
+    int32_t status;  // device error bits
+    int32_t pad;
+    uint64_t t_begin, t_end;  // device globaltimer
+    unsigned long long st[kStCount];
+    unsigned long long valid;
+};
+
+struct ServeCtl {  // device memory
+    int32_t exit_reason;
+    int32_t cmd;
+    int64_t head;        // next slot sequence number
+    int32_t stamp_next;  // stamps of the next request start here
+    int32_t pad;
+    unsigned long long grow_total;
+    ReqSlot cur;  // the request being applied (copied from the ring)
+};
+
+struct ServeArgs {
+    ReqSlot *ring;  // device pointer of the pinned ring
+    int32_t slots;
+    int64_t idle_ns;
+    ServeCtl *sc;
+    const double *powtab;
+};
+}  // namespace
+
+// Word-by-word copy that reads through volatile loads (the source may be host memory
+// the host is writing, or device memory written by another block).
+__device__ __forceinline__ void copy_slot(ReqSlot *dst, const ReqSlot *src) {
+    const volatile int32_t *sv = reinterpret_cast<const volatile int32_t *>(src);
+    int32_t *dv = reinterpret_cast<int32_t *>(dst);
+    for (int k = 0; k < (int)(sizeof(ReqSlot) / 4); ++k) dv[k] = sv[k];
+}
+
+__global__ void __launch_bounds__(512) k_serve(const __grid_constant__ GraphCtx base, const ServeArgs a) {
+    extern __shared__ int32_t sh[];
+    __shared__ GraphCtx gsh;
+    GridTeam T{base.ctl, base.wait_limit_ns, base.barrier_sleep_ns};
+    ServeCtl *sc = a.sc;
+    for (;;) {
+        // the leader waits for the next slot (bounded by the idle limit)
+        if (T.leader()) {
+            ReqSlot *r = a.ring + (sc->head % a.slots);
+            const uint64_t t0 = global_ns();
+            int32_t st;
+            while ((st = *(volatile int32_t *)&r->state) != kSlotReady && global_ns() - t0 < (uint64_t)a.idle_ns)
+                __nanosleep(256);
+            if (st == kSlotReady) {
+                __threadfence_system();
+                copy_slot(&sc->cur, r);
+                sc->cmd = 1;
+            } else {
+                sc->cmd = 0;
+                sc->exit_reason = kExitIdle;
+            }
+            __threadfence();
+        }
+        if (!T.sync()) return;
+        if (ld_volatile(&sc->cmd) == 0) return;
+        // a fresh control block and key set for this request (the barrier words stay)
+        {
+            int32_t *cw = reinterpret_cast<int32_t *>(base.ctl);
+            const int first = (int)(offsetof(Ctl, err) / 4);
+            for (int k = T.tid() + first; k < (int)(sizeof(Ctl) / 4); k += T.nthreads()) cw[k] = 0;
+            for (int64_t k = T.tid(); k < base.hcap; k += T.nthreads()) base.hset[k] = kEmptyKey;
+            for (int k = T.tid(); k <= base.K; k += T.nthreads()) base.bins[k] = 0;
+            if (sc->stamp_next + 2 * base.K + 8 >= 0x7fffffff) {  // stamps wrap: clear them
+                for (int k = T.tid(); k < base.n; k += T.nthreads()) base.stamp[k] = 0;
+            }
+        }
+        if (!T.sync()) return;
+        ReqSlot req;
+        copy_slot(&req, &sc->cur);
+        int32_t sbase = sc->stamp_next;
+        if (sbase + 2 * base.K + 8 >= 0x7fffffff) sbase = 1;
+        const uint64_t t_begin = global_ns();
+        if (req.op == kReqCoreness) {
+            for (int64_t v = T.tid(); v < base.n; v += T.nthreads()) {
+                int32_t g = -1;
+                if (base.deg[v] > 0) g = max((base.level[v] + 1) / base.Lg - 1, 0);
+                req.out[v] = g < 0 ? 0.0 : a.powtab[g];
+            }
+        } else {
+            if (threadIdx.x < (int)(sizeof(GraphCtx) / 4)) {
+                for (int k = threadIdx.x; k < (int)(sizeof(GraphCtx) / 4); k += blockDim.x)
+                    reinterpret_cast<int32_t *>(&gsh)[k] = reinterpret_cast<const int32_t *>(&base)[k];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                gsh.op = req.op == kReqInsert ? kOpInsert : kOpDelete;
+                gsh.edges = req.edges;
+                gsh.B = req.B;
+                gsh.stamp_base = sbase;
+            }
+            __syncthreads();
+            run_batch(T, gsh, sh, 0);
+        }
+        const bool ok = T.sync();
+        if (T.leader()) {
+            ReqSlot *r = a.ring + (sc->head % a.slots);
+            const int32_t err = ld_volatile(&base.ctl->err);
+            if (err == kErrNeedPool) {  // leave the slot ready; the host grows the pool and relaunches
+                sc->exit_reason = kExitNeedPool;
+                sc->grow_total = base.ctl->grow_total;
+                sc->stamp_next = sbase + base.K + 2;
+            } else {
+                r->status = err;
+                r->t_begin = t_begin;
+                r->t_end = global_ns();
+                for (int k = 0; k < kStCount; ++k) r->st[k] = base.ctl->st[k];
+                r->valid = base.ctl->vcount;
+                __threadfence_system();
+                *(volatile int32_t *)&r->state = kSlotDone;
+                sc->head += 1;
+                sc->stamp_next = sbase + base.K + 2;
+                if (err) sc->exit_reason = kExitError;
+            }
+            __threadfence();
+        }
+        if (!ok) return;
+        if (!T.sync()) return;
+    }
+}
+
+struct plds_server {
+    plds *h = nullptr;
+    int32_t slots = 0;
+    int64_t max_batch = 0;
+    ReqSlot *ring = nullptr;  // pinned, mapped
+    ReqSlot *ring_dev = nullptr;
+    std::vector<int32_t *> stage;  // pinned, mapped edge staging per slot
+    std::vector<int32_t *> stage_dev;
+    double *qbuf = nullptr;  // pinned, mapped coreness staging
+    double *qbuf_dev = nullptr;
+    std::vector<double *> qdest;  // where a finished query's values go (when staged)
+    DevBuf sc;
+    cudaStream_t run = nullptr;
+    cudaEvent_t done = nullptr;
+    bool running = false;
+    int64_t next_seq = 0;  // sequence number of the next submitted request
+    int64_t done_seq = 0;  // all sequence numbers below have been collected
+    int64_t idle_ns = 20ll * 1000 * 1000;
+    std::vector<plds_request_result> finished;
+};
+
+static int server_launch(plds_server *sv) {
+    plds *h = sv->h;
+    const int threads = block_threads(h);
+    const size_t smem = smem_bytes(threads);
+    static thread_local bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, threads, smem);
+    const int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : 1;
+    if (per_sm < 1) return PLDS_EDEVICE;
+    GraphCtx g = make_ctx(h, kOpInsert, nullptr, 0);
+    g.trace = nullptr;
+    g.trace_cap = 0;
+    // A loop that stopped on an error may have left grid-barrier arrivals counted
+    // (blocks leave a barrier early once the error word is set): start clean.
+    cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), sv->run);
+    cudaMemsetAsync(&P<ServeCtl>(sv->sc)->exit_reason, 0, sizeof(int32_t) * 2, sv->run);
+    ServeArgs a{sv->ring_dev, sv->slots, sv->idle_ns, P<ServeCtl>(sv->sc), P<double>(h->powtab)};
+    void *args[] = {(void *)&g, (void *)&a};
+    if (cudaLaunchCooperativeKernel((const void *)k_serve, dim3(h->num_sms * per_sm), dim3(threads), args, smem,
+                                    sv->run) != cudaSuccess) {
+        cudaGetLastError();
+        return PLDS_EDEVICE;
+    }
+    cudaEventRecord(sv->done, sv->run);
+    h->launches++;
+    sv->running = true;
+    return PLDS_OK;
+}
+
+// If the loop has stopped: read why, grow the pool if asked, relaunch when
+// requests are waiting.  Returns a status.
+static int server_service(plds_server *sv) {
+    if (!sv->running) return PLDS_OK;
+    if (cudaEventQuery(sv->done) == cudaErrorNotReady) return PLDS_OK;
+    cudaGetLastError();
+    sv->running = false;
+    plds *h = sv->h;
+    ServeCtl c{};
+    if (cudaMemcpy(&c, sv->sc.p, sizeof(ServeCtl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return PLDS_EDEVICE;
+    }
+    h->stamp_base = c.stamp_next;
+    Ctl hc{};
+    cudaMemcpy(&hc, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (hc.err & kErrTimeout) {
+        h->poisoned = true;
+        return PLDS_ETIMEOUT;
+    }
+    int32_t reset = kExitNone;
+    cudaMemcpy(&reinterpret_cast<ServeCtl *>(sv->sc.p)->exit_reason, &reset, 4, cudaMemcpyHostToDevice);
+    if (c.exit_reason == kExitNeedPool) {
+        int rc = grow_pool(h, (int64_t)c.grow_total);
+        if (rc) return rc;
+        cudaDeviceSynchronize();
+    }
+    if (sv->next_seq > c.head) return server_launch(sv);  // requests are waiting
+    return PLDS_OK;
+}
+
+// Move finished requests out of the ring; frees their slots.
+static void server_collect(plds_server *sv) {
+    while (sv->done_seq < sv->next_seq) {
+        ReqSlot *r = sv->ring + (sv->done_seq % sv->slots);
+        if (*(volatile int32_t *)&r->state != kSlotDone) break;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        plds_request_result out{};
+        out.ticket = r->ticket;
+        out.op = r->op;
+        out.status = r->status == 0 ? PLDS_OK : ((r->status & kErrInvalidId) ? PLDS_EINVAL : PLDS_EINTERNAL);
+        out.valid = (int64_t)r->valid;
+        out.rounds = (int64_t)r->st[kStRounds];
+        out.moves = (int64_t)r->st[kStMoves];
+        out.device_ns = (int64_t)(r->t_end - r->t_begin);
+        const int slot = (int)(sv->done_seq % sv->slots);
+        if (r->op == kReqCoreness && sv->qdest[slot]) {
+            std::memcpy(sv->qdest[slot], sv->qbuf, sizeof(double) * (size_t)sv->h->n);
+            sv->qdest[slot] = nullptr;
+        }
+        sv->finished.push_back(out);
+        *(volatile int32_t *)&r->state = kSlotFree;
+        sv->done_seq++;
+    }
+}
+
+static void server_free(plds_server *sv) {
+    if (sv->run) {
+        cudaStreamSynchronize(sv->run);
+        cudaStreamDestroy(sv->run);
+    }
+    if (sv->done) cudaEventDestroy(sv->done);
+    if (sv->ring) cudaFreeHost(sv->ring);
+    for (int32_t *p : sv->stage)
+        if (p) cudaFreeHost(p);
+    if (sv->qbuf) cudaFreeHost(sv->qbuf);
+    if (sv->h) dev_free(sv->h, sv->sc);
+    cudaGetLastError();
+    delete sv;
+}
+
+extern "C" plds_server_t *plds_server_create(plds_t *h, int32_t slots, int64_t max_batch) {
+    if (!h || slots < 1 || slots > 4096 || max_batch < 1) {
+        set_status(PLDS_EINVAL);
+        return nullptr;
+    }
+    if (h->poisoned) {
+        set_status(PLDS_EPOISONED);
+        return nullptr;
+    }
+    plds_server *sv = new (std::nothrow) plds_server();
+    if (!sv) {
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    sv->h = h;
+    sv->slots = slots;
+    sv->max_batch = max_batch;
+    cudaSetDevice(h->device);
+    bool ok = ensure_batch_scratch(h, max_batch) && dev_get(h, sv->sc, sizeof(ServeCtl)) &&
+              cudaStreamCreateWithFlags(&sv->run, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sv->done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaHostAlloc((void **)&sv->ring, sizeof(ReqSlot) * slots, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&sv->ring_dev, sv->ring, 0) == cudaSuccess &&
+              cudaHostAlloc((void **)&sv->qbuf, sizeof(double) * (size_t)h->n, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&sv->qbuf_dev, sv->qbuf, 0) == cudaSuccess;
+    if (ok) {
+        std::memset(sv->ring, 0, sizeof(ReqSlot) * slots);
+        sv->stage.assign(slots, nullptr);
+        sv->stage_dev.assign(slots, nullptr);
+        sv->qdest.assign(slots, nullptr);
+        for (int i = 0; i < slots && ok; ++i) {
+            ok = cudaHostAlloc((void **)&sv->stage[i], sizeof(int32_t) * 2 * (size_t)max_batch, cudaHostAllocMapped) ==
+                     cudaSuccess &&
+                 cudaHostGetDevicePointer((void **)&sv->stage_dev[i], sv->stage[i], 0) == cudaSuccess;
+        }
+    }
+    if (ok) {
+        ServeCtl c{};
+        c.stamp_next = h->stamp_base;
+        cudaStreamSynchronize(h->stream);
+        ok = cudaMemcpy(sv->sc.p, &c, sizeof(ServeCtl), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(h->ctl.p, 0, sizeof(Ctl)) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        server_free(sv);
+        set_status(PLDS_ENOMEM);
+        return nullptr;
+    }
+    set_status(PLDS_OK);
+    return sv;
+}
+
+extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *edges, int64_t B, double *out,
+                                  int64_t *ticket) {
+    if (!sv || op < kReqInsert || op > kReqCoreness) return set_status(PLDS_EINVAL);
+    if (op != kReqCoreness && (B < 0 || B > sv->max_batch || (B > 0 && !edges))) return set_status(PLDS_EINVAL);
+    if (op == kReqCoreness && !out) return set_status(PLDS_EINVAL);
+    plds *h = sv->h;
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    cudaSetDevice(h->device);
+    // wait for a free slot (collect finished requests, keep the loop alive)
+    const auto t0 = std::chrono::steady_clock::now();
+    while (sv->next_seq - sv->done_seq >= sv->slots) {
+        server_collect(sv);
+        int rc = server_service(sv);
+        if (rc) return set_status(rc);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(h->wait_limit_ns))
+            return set_status(PLDS_ETIMEOUT);
+    }
+    bool out_dev = false;
+    void *out_devptr = nullptr;
+    if (op == kReqCoreness) {
+        cudaPointerAttributes pa{};
+        out_dev = cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.devicePointer &&
+                  (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged || pa.type == cudaMemoryTypeHost);
+        out_devptr = pa.devicePointer;
+        cudaGetLastError();
+        // pageable output goes through the one staging buffer: one such query at a time
+        while (!out_dev && std::any_of(sv->qdest.begin(), sv->qdest.end(), [](double *d) { return d != nullptr; })) {
+            server_collect(sv);
+            int rc = server_service(sv);
+            if (rc) return set_status(rc);
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(h->wait_limit_ns))
+                return set_status(PLDS_ETIMEOUT);
+        }
+    }
+    const int slot = (int)(sv->next_seq % sv->slots);
+    ReqSlot *r = sv->ring + slot;
+    r->op = op;
+    r->B = op == kReqCoreness ? 0 : B;
+    r->ticket = sv->next_seq;
+    r->edges = nullptr;
+    r->out = nullptr;
+    if (op != kReqCoreness && B > 0) {
+        cudaPointerAttributes pa{};
+        const bool dev = cudaPointerGetAttributes(&pa, edges) == cudaSuccess && pa.devicePointer &&
+                         (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged ||
+                          pa.type == cudaMemoryTypeHost);
+        cudaGetLastError();
+        if (dev) {
+            r->edges = static_cast<const int32_t *>(pa.devicePointer);
+        } else {  // pageable memory: copy into the slot's pinned staging
+            std::memcpy(sv->stage[slot], edges, sizeof(int32_t) * 2 * (size_t)B);
+            r->edges = sv->stage_dev[slot];
+        }
+    }
+    if (op == kReqCoreness) {
+        r->out = out_dev ? static_cast<double *>(out_devptr) : sv->qbuf_dev;
+        sv->qdest[slot] = out_dev ? nullptr : out;
+    }
+    std::atomic_thread_fence(std::memory_order_release);
+    *(volatile int32_t *)&r->state = kSlotReady;
+    if (ticket) *ticket = sv->next_seq;
+    sv->next_seq++;
+    int rc = server_service(sv);
+    if (rc) return set_status(rc);
+    if (!sv->running) {
+        rc = server_launch(sv);
+        if (rc) return set_status(rc);
+    }
+    return set_status(PLDS_OK);
+}
+
+extern "C" int plds_server_poll(plds_server_t *sv, plds_request_result *out, int32_t cap) {
+    if (!sv || (cap > 0 && !out) || cap < 0) return set_status(PLDS_EINVAL);
+    server_collect(sv);
+    int rc = server_service(sv);
+    if (rc) return set_status(rc);
+    const int32_t k = std::min<int32_t>(cap, (int32_t)sv->finished.size());
+    for (int32_t i = 0; i < k; ++i) out[i] = sv->finished[i];
+    sv->finished.erase(sv->finished.begin(), sv->finished.begin() + k);
+    set_status(PLDS_OK);
+    return k;
+}
+
+extern "C" int plds_server_drain(plds_server_t *sv) {
+    if (!sv) return set_status(PLDS_EINVAL);
+    const auto t0 = std::chrono::steady_clock::now();
+    while (sv->done_seq < sv->next_seq) {
+        server_collect(sv);
+        int rc = server_service(sv);
+        if (rc) return set_status(rc);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(sv->h->wait_limit_ns))
+            return set_status(PLDS_ETIMEOUT);
+    }
+    return set_status(PLDS_OK);
+}
+
+extern "C" void plds_server_destroy(plds_server_t *sv) {
+    if (!sv) return;
+    plds_server_drain(sv);
+    // wait for the loop to go idle and exit
+    if (sv->running) cudaEventSynchronize(sv->done);
+    sv->running = false;
+    ServeCtl c{};
+    if (cudaMemcpy(&c, sv->sc.p, sizeof(ServeCtl), cudaMemcpyDeviceToHost) == cudaSuccess)
+        sv->h->stamp_base = c.stamp_next;
+    cudaGetLastError();
+    server_free(sv);
 }

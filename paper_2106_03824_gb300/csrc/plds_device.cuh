@@ -204,6 +204,7 @@ __device__ __forceinline__ bool table_erase(int32_t *slots, int64_t off, int32_t
 
 __device__ __forceinline__ int4 empty4() { return make_int4(kEmpty, kEmpty, kEmpty, kEmpty); }
 
+
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     x ^= x >> 33;
     x *= 0xff51afd7ed558ccdull;
@@ -222,6 +223,10 @@ __device__ __forceinline__ int32_t next_pow2(int64_t x) {
 
 __device__ __forceinline__ int32_t sid_of(const GraphCtx &g, int32_t l) { return g.stamp_base + 1 + l; }
 
+// A neighbour id read from a table; anything outside [0,n) other than the empty
+// and tombstone marks would be a corrupted slot, which is never dereferenced.
+__device__ __forceinline__ bool valid_id(const GraphCtx &g, int32_t w) { return (uint32_t)w < (uint32_t)g.n; }
+
 // Record an error bit and, for the first error only, which check raised it.
 __device__ __forceinline__ void report(const GraphCtx &g, int32_t bit, int32_t site, int32_t a = 0,
                                       int32_t b = 0, int32_t c = 0) {
@@ -231,6 +236,15 @@ __device__ __forceinline__ void report(const GraphCtx &g, int32_t bit, int32_t s
         g.ctl->err_info[2] = c;
     }
     atomicOr(&g.ctl->err, bit);
+}
+
+// A scan item must name a vertex and a table inside the pool; a corrupted item is
+// reported and skipped instead of being dereferenced.
+__device__ __forceinline__ bool item_ok(const GraphCtx &g, const int4 &it, int lg) {
+    const bool ok = (uint32_t)it.x < (uint32_t)g.n && lg >= 2 && lg <= 30 && it.z >= 0 &&
+                    4 * (int64_t)it.z + ((int64_t)1 << lg) <= g.pool_cap;
+    if (!ok) report(g, kErrInternal, 10, it.x, lg, it.z);
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -874,7 +888,7 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
 // up*-neighbour.  Returns true if w must be pushed to the next frontier.
 __device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t snext,
                                            int &cnt_l) {
-    if (w < 0 || (raw & kMoveFlag)) return false;  // empty slot, or w moved up in this round as well
+    if (!valid_id(g, w) || (raw & kMoveFlag)) return false;  // empty slot, or w moved up in this round as well
     if (raw == l) {
         cnt_l++;
     } else if (raw == l + 1) {
@@ -986,7 +1000,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
         for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
             const int i = i0 + lane;
             const int4 it = i < tlc ? g.TL[p][i] : make_int4(0, 0, 0, 0);
-            const int ng = i < tlc ? (1 << it.y) >> 2 : 0;
+            const int ng = (i < tlc && item_ok(g, it, it.y)) ? (1 << it.y) >> 2 : 0;
             const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
             int cnt_l = 0;
             for (int j0 = 0; j0 < maxg; j0 += 4) {
@@ -997,7 +1011,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+                for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
                 unsigned push = 0;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -1020,12 +1034,12 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 const int cu = c0 + u * T.nwarps();
                 it[u] = cu < clc ? g.CL[p][cu] : make_int4(0, 0, 0, 0);
                 const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
-                in[u] = cu < clc && j < ((1 << (it[u].y & 31)) >> 2);
+                in[u] = cu < clc && item_ok(g, it[u], it[u].y & 31) && j < ((1 << (it[u].y & 31)) >> 2);
                 const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
                 ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
             }
 #pragma unroll
-            for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+            for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
             int cl4[4] = {0, 0, 0, 0};
             unsigned push = 0;
 #pragma unroll
@@ -1310,7 +1324,7 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
 // pending (its dlv decides).
 __device__ __forceinline__ int del_effect(const GraphCtx &g, int32_t w, int32_t lw, int32_t l, int32_t pv, int &cu,
                                           int &cs) {
-    if (w < 0) return 0;
+    if (!valid_id(g, w)) return 0;
     cu += lw >= l;
     cs += lw >= l - 1;
     if (lw <= l) return 0;
@@ -1407,7 +1421,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
         for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
             const int i = i0 + lane;
             const int4 it = i < tlc ? g.TL[0][i] : make_int4(0, 0, 0, 0);
-            const int ng = i < tlc ? (1 << it.y) >> 2 : 0;
+            const int ng = (i < tlc && item_ok(g, it, it.y)) ? (1 << it.y) >> 2 : 0;
             const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
             int cu = 0, cs = 0;
             for (int j0 = 0; j0 < maxg; j0 += 4) {
@@ -1418,7 +1432,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
                     ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+                for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
                 unsigned push = 0, maybe = 0;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -1451,12 +1465,12 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
                 const int cu = c0 + u * T.nwarps();
                 it[u] = cu < clc ? g.CL[0][cu] : make_int4(0, 0, 0, 0);
                 const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
-                in[u] = cu < clc && j < ((1 << (it[u].y & 31)) >> 2);
+                in[u] = cu < clc && item_ok(g, it[u], it[u].y & 31) && j < ((1 << (it[u].y & 31)) >> 2);
                 const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
                 ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
             }
 #pragma unroll
-            for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : 0;
+            for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
             int cu4[4] = {0, 0, 0, 0}, cs4[4] = {0, 0, 0, 0};
             unsigned push = 0, maybe = 0;
 #pragma unroll

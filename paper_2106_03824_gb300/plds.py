@@ -49,6 +49,12 @@ class PldsTuning(ctypes.Structure):
                 ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32)]
 
 
+class RequestResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("op", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("valid", ctypes.c_int64), ("rounds", ctypes.c_int64), ("moves", ctypes.c_int64),
+                ("device_ns", ctypes.c_int64)]
+
+
 class PldsError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: PLDS_{_NAMES.get(code, code)} ({code})")
@@ -92,6 +98,13 @@ def load():
     L.plds_set_graph.argtypes = [vp, i32]
     L.plds_set_destroy.argtypes = [vp]
     L.plds_set_destroy.restype = None
+    L.plds_server_create.restype = vp
+    L.plds_server_create.argtypes = [vp, i32, i64]
+    L.plds_server_submit.argtypes = [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.plds_server_poll.argtypes = [vp, ctypes.POINTER(RequestResult), i32]
+    L.plds_server_drain.argtypes = [vp]
+    L.plds_server_destroy.argtypes = [vp]
+    L.plds_server_destroy.restype = None
     L.plds_last_status.argtypes = []
     L.plds_destroy.argtypes = [vp]
     L.plds_destroy.restype = None
@@ -299,6 +312,63 @@ class PLDSSet:
                 g._h = None
             load().plds_set_destroy(self._s)
             self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Device-resident request loop over one PLDS graph (serving form)."""
+    INSERT, DELETE, CORENESS = 0, 1, 2
+
+    def __init__(self, graph: "PLDS", slots: int = 8, max_batch: int = 1 << 20):
+        self.g = graph
+        self._sv = load().plds_server_create(graph._h, int(slots), int(max_batch))
+        if not self._sv:
+            raise PldsError(load().plds_last_status(), "plds_server_create")
+        self._keep = {}  # buffers that must stay alive until their request finishes
+
+    def submit(self, op: int, edges=None, out=None) -> int:
+        t = ctypes.c_int64()
+        if op == self.CORENESS:
+            rc = load().plds_server_submit(self._sv, op, None, 0, _ptr(out), ctypes.byref(t))
+        else:
+            if isinstance(edges, np.ndarray):
+                edges = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+            elif getattr(edges, "is_cuda", False):
+                # the loop reads device buffers in place: their producing work must be done
+                __import__("torch").cuda.current_stream().synchronize()
+            rc = load().plds_server_submit(self._sv, op, _ptr(edges), int(edges.shape[0]), None,
+                                           ctypes.byref(t))
+        if rc != PLDS_OK:
+            raise PldsError(rc, "plds_server_submit")
+        self._keep[t.value] = (edges, out)
+        return t.value
+
+    def poll(self, cap: int = 1024):
+        buf = (RequestResult * cap)()
+        k = load().plds_server_poll(self._sv, buf, cap)
+        if k < 0:
+            raise PldsError(k, "plds_server_poll")
+        res = [dict(ticket=r.ticket, op=r.op, status=r.status, valid=r.valid, rounds=r.rounds,
+                    moves=r.moves, device_ns=r.device_ns) for r in buf[:k]]
+        for r in res:
+            self._keep.pop(r["ticket"], None)
+        return res
+
+    def drain(self):
+        rc = load().plds_server_drain(self._sv)
+        if rc != PLDS_OK:
+            raise PldsError(rc, "plds_server_drain")
+
+    def close(self):
+        if getattr(self, "_sv", None):
+            load().plds_server_destroy(self._sv)
+            self._sv = None
+            self._keep.clear()
 
     def __del__(self):
         try:
