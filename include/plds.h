@@ -222,42 +222,79 @@ void plds_set_destroy(plds_set_t *s);
 /*
  * Serving form: a device-resident request loop over one graph (the paper has no
  * counterpart).  One persistent kernel applies requests from a ring of `slots`
- * slots in pinned host memory, strictly in submission order and with unchanged
- * batch boundaries, so the graph ends exactly as if each request had been its own
- * plds_batch_insert / plds_batch_delete call; coreness queries in between see the
- * state after every earlier request.  While a server is open on a handle, use
- * only the server calls on that handle.
- *   plds_server_create: slots in the ring; max_batch = largest batch (edges).
+ * slots in pinned host memory, in submission order; coreness queries see the state
+ * after every earlier request.  While a server is open on a handle, use only the
+ * server calls on that handle.
+ *
+ * Continuous batching: requests that wait in the ring while the device works are
+ * admitted together -- the loop applies a run of consecutive insertion requests
+ * (or deletion requests) as ONE batch of at most `merge_max_edges` edges and 64
+ * requests.  Every request of such a batch reports the batch's first ticket and
+ * its number of requests (batch_first, batch_size), so the schedule can be
+ * replayed batch by batch (for instance by a sequential implementation applying
+ * the concatenated edges as one batch).  Merging changes which levels the
+ * vertices end on, not the edge set, and every estimate keeps the (2+eps)
+ * approximation bound (Section "Batch-Dynamic k-Core Decomposition", the
+ * approximation lemma on the coreness estimate).  A request holding an id outside [0, n) is rejected alone
+ * (status PLDS_EINVAL, nothing of it applied); the other requests of its batch are
+ * applied.  With merge_max_edges = 0 every request is its own batch, and the
+ * graph ends exactly as if each request had been its own plds_batch_insert /
+ * plds_batch_delete call.
+ *
+ * Admission: a request is admitted when a ring slot is free and, for an insertion
+ * of B edges, the adjacency can take its worst case (both endpoint tables of every
+ * edge doubling: ceil(4 B den / num) slots at load num/den), either in the pool as
+ * it is or in a grown pool that fits in free device memory (1 GiB kept free) and
+ * in the pool limit.  Otherwise submit waits for admitted requests to finish, or
+ * returns PLDS_ENOMEM (nothing admitted) when none is left to wait for.
+ *
+ *   plds_server_create: slots in the ring (1..4096); max_batch = largest batch
+ *     (edges) of one request and of one merged batch.  Merging starts enabled
+ *     with merge_max_edges = max_batch.
+ *   plds_server_configure: merge_max_edges (0 = unchanged boundaries, -1 =
+ *     max_batch; larger values are clamped to max_batch) and pool_limit_bytes
+ *     (0 = no limit beyond free device memory).  Applies to requests submitted
+ *     afterwards.
  *   plds_server_submit: op 0 insertion batch, 1 deletion batch, 2 coreness query
  *     (out = double[n], host or device; edges ignored).  Edge arrays may be device
  *     memory or pinned host memory (read in place by the running loop: their
  *     contents must be complete at submission -- no copy still in flight on a
  *     stream -- and unchanged until the request has finished) or pageable host
- *     memory (copied at submission).  Blocks
- *     only while every slot is busy.  *ticket gets the request's number (0, 1, ...).
+ *     memory (copied at submission).  Blocks only while every slot is busy or
+ *     admission waits.  *ticket gets the request's number (0, 1, ...).
  *   plds_server_poll: copies up to cap finished requests into out (oldest first);
  *     returns their count or a negative code.
  *   plds_server_drain: waits until every submitted request has finished.
  *   plds_server_destroy: drains, stops the loop, frees the server (not the graph).
- * Pool growth is gated by free device memory (1 GiB kept free); a request that
- * cannot get room finishes with PLDS_ENOMEM reported by the call that noticed it.
+ *   plds_server_admission: the admission rule above as a pure function (no device
+ *     use): pool_cap, pool_used, inflight (slots promised to admitted requests) and
+ *     need in adjacency slots, free_bytes the device memory a grown pool may take.
+ *     Returns 0 admit, 1 wait for admitted requests, 2 reject, or PLDS_EINVAL for a
+ *     negative argument.
  */
 typedef struct plds_server plds_server_t;
 typedef struct plds_request_result {
     int64_t ticket;
     int32_t op;
     int32_t status;     /* PLDS_OK or a PLDS_E* code */
-    int64_t valid;      /* updates applied */
-    int64_t rounds;
-    int64_t moves;
-    int64_t device_ns;  /* time the device spent on the request */
+    int64_t valid;      /* updates applied by the request's batch */
+    int64_t rounds;     /* of the request's batch */
+    int64_t moves;      /* of the request's batch */
+    int64_t device_ns;  /* time the device spent on the request's batch */
+    int64_t batch_first;  /* ticket of the first request of the batch it was applied in */
+    int32_t batch_size;   /* requests in that batch (1 when not merged) */
+    int32_t pad;
+    int64_t done_ns;      /* CLOCK_MONOTONIC time at which the host saw it finish */
 } plds_request_result;
 plds_server_t *plds_server_create(plds_t *h, int32_t slots, int64_t max_batch);
+int plds_server_configure(plds_server_t *sv, int64_t merge_max_edges, int64_t pool_limit_bytes);
 int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *edges, int64_t B, double *out,
                        int64_t *ticket);
 int plds_server_poll(plds_server_t *sv, plds_request_result *out, int32_t cap);
 int plds_server_drain(plds_server_t *sv);
 void plds_server_destroy(plds_server_t *sv);
+int plds_server_admission(int64_t pool_cap, int64_t pool_used, int64_t inflight, int64_t need,
+                          int64_t free_bytes);
 
 /* Status code of the calling thread's last call. */
 int plds_last_status(void);

@@ -16,6 +16,7 @@
 #include <mutex>
 #include <thread>
 #include <new>
+#include <time.h>
 #include <vector>
 
 #include "plds.h"
@@ -37,7 +38,7 @@ static int set_status(int s) {
 __global__ void __launch_bounds__(512) k_batch_grid(const __grid_constant__ GraphCtx g) {
     extern __shared__ int32_t sh[];
     GridTeam T{g.ctl, g.wait_limit_ns, g.barrier_sleep_ns};
-    run_batch(T, g, sh, 0);
+    run_batch(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh, 0);
 }
 
 // Coreness estimate (Definition "Coreness Estimate"): exponent
@@ -146,6 +147,8 @@ struct plds {
     DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, inc;
     DevBuf pool, pool_top, ctl;
     int64_t pool_cap = 0;
+    int64_t pool_live = 0;   // slots in use after the last compaction
+    int64_t pool_limit = 0;  // bytes a grown pool may take (0: free HBM only)
     // scratch: n-sized
     DevBuf F[2], M[2], TL[2], P[2], R, R2, bins, levlist, CL[2];
     int64_t clcap = 0;
@@ -260,6 +263,9 @@ static size_t smem_bytes(int threads, int stage_shift = 0) {
            (size_t)(2 * kMaxGroups + 64 + kWarpHist + 32 + (threads / 32) * kWarpHist + stage_ints(stage_shift));
 }
 
+// Device memory that pool growth and serving admission leave free for everything else.
+constexpr int64_t kHbmReserve = 1ll << 30;
+
 // Move every table into a new pool laid out back to back, with room for `extra`
 // more slots; the old pool is freed.
 static int grow_pool(plds *h, int64_t extra) {
@@ -284,11 +290,17 @@ static int grow_pool(plds *h, int64_t extra) {
     if (rc) return rc;
     int64_t want = std::max<int64_t>(h->pool_cap, 2 * (live + extra));
     want = (want + 3) & ~(int64_t)3;
-    // gate on free HBM: keep 1 GiB free for everything else on the device
+    // gate on free HBM (keep kHbmReserve free for everything else on the device)
+    // and on the pool limit, if one is set
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
-        (int64_t)free_b - (int64_t)(1ll << 30) < 4 * want) {
-        const int64_t fit = ((int64_t)free_b - (int64_t)(1ll << 30)) / 4;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    int64_t avail = (int64_t)free_b - kHbmReserve;
+    if (h->pool_limit > 0) avail = std::min<int64_t>(avail, h->pool_limit);
+    if (avail < 4 * want) {
+        const int64_t fit = avail / 4;
         want = std::max<int64_t>(live + extra + 4, fit) & ~(int64_t)3;
         if (want < live + extra) {
             dev_free(h, bsum);
@@ -320,6 +332,7 @@ static int grow_pool(plds *h, int64_t extra) {
     dev_free(h, h->pool);
     h->pool = np;
     h->pool_cap = want;
+    h->pool_live = live;
     h->pool_grows++;
     dev_free(h, bsum);
     dev_free(h, newoff);
@@ -911,7 +924,7 @@ __global__ void __launch_bounds__(kSetThreads, 2)
                 for (int k = threadIdx.x; k <= gsh.K; k += blockDim.x) gsh.bins[k] = 0;
             __syncthreads();
             BlockTeam T{gsh.ctl};
-            run_batch(T, gsh, sh, kSetStageShift);
+            run_batch(T, gsh, BatchIn{gsh.edges, gsh.B, gsh.op, gsh.stamp_base}, sh, kSetStageShift);
             __syncthreads();
             if (ld_volatile(&gsh.ctl->err) != 0) break;  // the host resolves it and reruns this graph
         }
@@ -1161,18 +1174,29 @@ extern "C" void plds_set_destroy(plds_set_t *s) {
 // pinned host memory that the device reads directly; the kernel's leader thread
 // polls the next slot, the grid applies the request with the same routines as a
 // single batch call, and the leader writes the completion record back into the
-// slot.  Requests are applied strictly in submission order with unchanged
-// boundaries, so the graph ends up exactly as if each request had been a
-// separate call.  The host admits a new request whenever a slot is free: its
+// slot.  Requests are applied in submission order.  The host admits a new
+// request whenever a slot is free and the adjacency could grow to hold it: its
 // copy-in overlaps with the device working on earlier requests, and no kernel
-// launch or host synchronisation sits between requests.  The loop exits after
-// an idle period or when the adjacency pool needs to grow (the host grows it,
-// gated by free HBM, and relaunches).
+// launch or host synchronisation sits between requests.
+//
+// Continuous batching: when the leader finds several consecutive update
+// requests of the same kind already waiting, it applies them as ONE batch (up
+// to merge_cap edges, at most kMaxSeg requests): the grid gathers their edges
+// into one device buffer, validating ids per request so that a request with an
+// id out of range is rejected alone.  Every merged request's completion names
+// the first ticket and the number of requests of the batch it went into, so the
+// schedule can be replayed batch by batch.  With merge_cap 0 every request is
+// its own batch (unchanged boundaries).  Queries are never merged: they see the
+// state after every earlier request.
+//
+// The loop exits after an idle period or when the adjacency pool needs to grow
+// (the host grows it, gated by free HBM, and relaunches).
 // ---------------------------------------------------------------------------
 namespace {
 enum : int32_t { kSlotFree = 0, kSlotReady = 1, kSlotDone = 2 };
 enum : int32_t { kReqInsert = 0, kReqDelete = 1, kReqCoreness = 2 };
 enum : int32_t { kExitNone = 0, kExitIdle = 1, kExitNeedPool = 2, kExitError = 3 };
+constexpr int kMaxSeg = 64;  // requests merged into one batch at most
 
 struct alignas(64) ReqSlot {
     int32_t state;  // kSlot*
@@ -1181,10 +1205,13 @@ struct alignas(64) ReqSlot {
     const int32_t *edges;  // device-accessible
     double *out;           // device-accessible (coreness queries)
     int64_t ticket;
+    int64_t merge_cap;  // edges one merged batch may hold (0: never merge)
     // written by the device
-    int32_t status;  // device error bits
-    int32_t pad;
+    int32_t status;   // device error bits
+    int32_t batch_n;  // requests in the batch this one was applied in
+    int64_t batch_first;  // ticket of that batch's first request
     uint64_t t_begin, t_end;  // device globaltimer
+    unsigned long long pool_top;  // adjacency slots handed out after the request
     unsigned long long st[kStCount];
     unsigned long long valid;
 };
@@ -1194,9 +1221,13 @@ struct ServeCtl {  // device memory
     int32_t cmd;
     int64_t head;        // next slot sequence number
     int32_t stamp_next;  // stamps of the next request start here
-    int32_t pad;
+    int32_t nseg;        // requests in the current batch (0: a query or an unmerged request)
     unsigned long long grow_total;
-    ReqSlot cur;  // the request being applied (copied from the ring)
+    int64_t seg_total;   // edges gathered (after rejected requests are dropped)
+    ReqSlot cur;         // the head request (copied from the ring)
+    const int2 *seg_ptr[kMaxSeg];
+    int64_t seg_off[kMaxSeg + 1];
+    int32_t seg_bad[kMaxSeg];
 };
 
 struct ServeArgs {
@@ -1205,6 +1236,7 @@ struct ServeArgs {
     int64_t idle_ns;
     ServeCtl *sc;
     const double *powtab;
+    int2 *ebuf;  // gathered edges of a merged batch [max_batch]
 };
 }  // namespace
 
@@ -1216,9 +1248,57 @@ __device__ __forceinline__ void copy_slot(ReqSlot *dst, const ReqSlot *src) {
     for (int k = 0; k < (int)(sizeof(ReqSlot) / 4); ++k) dv[k] = sv[k];
 }
 
+// Leader: extend the batch that starts with the head request by the waiting
+// requests that follow it (same kind, total edges within the cap).
+__device__ void serve_select(const ServeArgs &a, ServeCtl *sc) {
+    const ReqSlot &c = sc->cur;
+    sc->nseg = 0;
+    if (c.op == kReqCoreness || c.merge_cap <= 0 || c.B > c.merge_cap) return;
+    int64_t total = c.B;
+    sc->seg_ptr[0] = reinterpret_cast<const int2 *>(c.edges);
+    sc->seg_off[0] = 0;
+    sc->seg_bad[0] = 0;
+    int ns = 1;
+    for (int j = 1; j < a.slots && ns < kMaxSeg; ++j) {
+        const ReqSlot *r = a.ring + ((sc->head + j) % a.slots);
+        if (*(volatile const int32_t *)&r->state != kSlotReady) break;
+        __threadfence_system();
+        const int32_t op = *(volatile const int32_t *)&r->op;
+        const int64_t B = *(volatile const int64_t *)&r->B;
+        if (op != c.op || total + B > c.merge_cap) break;
+        sc->seg_ptr[ns] = reinterpret_cast<const int2 *>(*(const int32_t *volatile *)&r->edges);
+        sc->seg_off[ns] = total;
+        sc->seg_bad[ns] = 0;
+        total += B;
+        ++ns;
+    }
+    sc->seg_off[ns] = total;
+    sc->seg_total = total;
+    sc->nseg = ns > 1 ? ns : 0;  // a request alone is read in place
+}
+
+// Grid: copy the batch's requests into one contiguous edge array; with `check`,
+// flag each request holding an id outside [0, n).  Segment offsets are in shared
+// memory (s_off[0..ns]).
+__device__ void serve_gather(GridTeam &T, const ServeCtl *sc, int ns, const int64_t *s_off, int2 *ebuf, int32_t n,
+                             bool check, int32_t *bad) {
+    const int64_t total = s_off[ns];
+    for (int64_t i = T.tid(); i < total; i += T.nthreads()) {
+        int lo = 0, hi = ns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int2 uv = sc->seg_ptr[lo][i - s_off[lo]];
+        if (check && (uv.x < 0 || uv.x >= n || uv.y < 0 || uv.y >= n)) *(volatile int32_t *)&bad[lo] = 1;
+        ebuf[i] = uv;
+    }
+}
+
 __global__ void __launch_bounds__(512) k_serve(const __grid_constant__ GraphCtx base, const ServeArgs a) {
     extern __shared__ int32_t sh[];
-    __shared__ GraphCtx gsh;
+    __shared__ int64_t s_off[kMaxSeg + 1];
     GridTeam T{base.ctl, base.wait_limit_ns, base.barrier_sleep_ns};
     ServeCtl *sc = a.sc;
     for (;;) {
@@ -1232,6 +1312,7 @@ __global__ void __launch_bounds__(512) k_serve(const __grid_constant__ GraphCtx 
             if (st == kSlotReady) {
                 __threadfence_system();
                 copy_slot(&sc->cur, r);
+                serve_select(a, sc);
                 sc->cmd = 1;
             } else {
                 sc->cmd = 0;
@@ -1252,9 +1333,34 @@ __global__ void __launch_bounds__(512) k_serve(const __grid_constant__ GraphCtx 
                 for (int k = T.tid(); k < base.n; k += T.nthreads()) base.stamp[k] = 0;
             }
         }
-        if (!T.sync()) return;
         ReqSlot req;
         copy_slot(&req, &sc->cur);
+        const int ns = ld_volatile(&sc->nseg);
+        if (ns > 0) {  // gather the batch's requests, rejecting those with a bad id
+            for (int k = threadIdx.x; k <= ns; k += blockDim.x) s_off[k] = sc->seg_off[k];
+            __syncthreads();
+            serve_gather(T, sc, ns, s_off, a.ebuf, base.n, true, sc->seg_bad);
+            if (!T.sync()) return;
+            bool anybad = false;
+            for (int k = 0; k < ns; ++k) anybad |= ld_volatile(&sc->seg_bad[k]) != 0;
+            if (anybad) {  // gather again without the rejected requests (they keep length 0)
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int64_t t = 0;
+                    for (int k = 0; k < ns; ++k) {
+                        s_off[k] = t;
+                        if (!ld_volatile(&sc->seg_bad[k])) t += sc->seg_off[k + 1] - sc->seg_off[k];
+                    }
+                    s_off[ns] = t;
+                }
+                __syncthreads();
+                if (T.leader()) sc->seg_total = s_off[ns];
+                // a zero-length segment is never selected by the search below (offsets
+                // equal), so the remaining requests' edges land contiguously
+                serve_gather(T, sc, ns, s_off, a.ebuf, base.n, false, sc->seg_bad);
+            }
+        }
+        if (!T.sync()) return;
         int32_t sbase = sc->stamp_next;
         if (sbase + 2 * base.K + 8 >= 0x7fffffff) sbase = 1;
         const uint64_t t_begin = global_ns();
@@ -1265,37 +1371,37 @@ __global__ void __launch_bounds__(512) k_serve(const __grid_constant__ GraphCtx 
                 req.out[v] = g < 0 ? 0.0 : a.powtab[g];
             }
         } else {
-            if (threadIdx.x < (int)(sizeof(GraphCtx) / 4)) {
-                for (int k = threadIdx.x; k < (int)(sizeof(GraphCtx) / 4); k += blockDim.x)
-                    reinterpret_cast<int32_t *>(&gsh)[k] = reinterpret_cast<const int32_t *>(&base)[k];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                gsh.op = req.op == kReqInsert ? kOpInsert : kOpDelete;
-                gsh.edges = req.edges;
-                gsh.B = req.B;
-                gsh.stamp_base = sbase;
-            }
-            __syncthreads();
-            run_batch(T, gsh, sh, 0);
+            const BatchIn in{ns > 0 ? reinterpret_cast<const int32_t *>(a.ebuf) : req.edges,
+                             ns > 0 ? *(volatile const int64_t *)&sc->seg_total : req.B,
+                             req.op == kReqInsert ? kOpInsert : kOpDelete, sbase};
+            run_batch(T, base, in, sh, 0);
         }
         const bool ok = T.sync();
         if (T.leader()) {
-            ReqSlot *r = a.ring + (sc->head % a.slots);
             const int32_t err = ld_volatile(&base.ctl->err);
-            if (err == kErrNeedPool) {  // leave the slot ready; the host grows the pool and relaunches
+            if (err == kErrNeedPool) {  // leave the slots ready; the host grows the pool and relaunches
                 sc->exit_reason = kExitNeedPool;
                 sc->grow_total = base.ctl->grow_total;
                 sc->stamp_next = sbase + base.K + 2;
             } else {
-                r->status = err;
-                r->t_begin = t_begin;
-                r->t_end = global_ns();
-                for (int k = 0; k < kStCount; ++k) r->st[k] = base.ctl->st[k];
-                r->valid = base.ctl->vcount;
+                const int nr = ns > 0 ? ns : 1;
+                const uint64_t t_end = global_ns();
+                const unsigned long long top = *(volatile unsigned long long *)base.pool_top;
+                for (int j = 0; j < nr; ++j) {
+                    ReqSlot *r = a.ring + ((sc->head + j) % a.slots);
+                    r->status = (ns > 0 && ld_volatile(&sc->seg_bad[j])) ? kErrInvalidId : err;
+                    r->batch_n = nr;
+                    r->batch_first = req.ticket;
+                    r->t_begin = t_begin;
+                    r->t_end = t_end;
+                    r->pool_top = top;
+                    for (int k = 0; k < kStCount; ++k) r->st[k] = base.ctl->st[k];
+                    r->valid = base.ctl->vcount;
+                }
                 __threadfence_system();
-                *(volatile int32_t *)&r->state = kSlotDone;
-                sc->head += 1;
+                for (int j = 0; j < nr; ++j)
+                    *(volatile int32_t *)&a.ring[(sc->head + j) % a.slots].state = kSlotDone;
+                sc->head += nr;
                 sc->stamp_next = sbase + base.K + 2;
                 if (err) sc->exit_reason = kExitError;
             }
@@ -1314,18 +1420,38 @@ struct plds_server {
     ReqSlot *ring_dev = nullptr;
     std::vector<int32_t *> stage;  // pinned, mapped edge staging per slot
     std::vector<int32_t *> stage_dev;
+    std::vector<int64_t> stage_cap;  // edges; allocated on first use by a pageable input
     double *qbuf = nullptr;  // pinned, mapped coreness staging
     double *qbuf_dev = nullptr;
     std::vector<double *> qdest;  // where a finished query's values go (when staged)
-    DevBuf sc;
+    DevBuf sc, ebuf;
     cudaStream_t run = nullptr;
     cudaEvent_t done = nullptr;
     bool running = false;
     int64_t next_seq = 0;  // sequence number of the next submitted request
     int64_t done_seq = 0;  // all sequence numbers below have been collected
     int64_t idle_ns = 20ll * 1000 * 1000;
+    int64_t merge_cap = 0;        // edges per merged batch (0: unchanged boundaries)
+    int64_t pool_limit = 0;       // bytes the adjacency pool may take (0: free HBM only)
+    int64_t pool_used = 0;        // adjacency slots handed out, as last reported
+    int64_t inflight_need = 0;    // worst-case slots of admitted, unfinished insertions
+    std::vector<int64_t> need;    // per ring slot
     std::vector<plds_request_result> finished;
 };
+
+static int64_t now_monotonic_ns() {
+    timespec ts{};
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
+// Worst-case adjacency slots an insertion batch of B edges can take: both endpoint
+// tables may double, at load num/den.
+static int64_t insert_need_slots(const plds *h, int64_t B) {
+    const int64_t num = h->tune.load_num > 0 ? h->tune.load_num : 3;
+    const int64_t den = h->tune.load_den > 0 ? h->tune.load_den : 4;
+    return (4 * B * den + num - 1) / num;
+}
 
 static int server_launch(plds_server *sv) {
     plds *h = sv->h;
@@ -1347,7 +1473,7 @@ static int server_launch(plds_server *sv) {
     // (blocks leave a barrier early once the error word is set): start clean.
     cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), sv->run);
     cudaMemsetAsync(&P<ServeCtl>(sv->sc)->exit_reason, 0, sizeof(int32_t) * 2, sv->run);
-    ServeArgs a{sv->ring_dev, sv->slots, sv->idle_ns, P<ServeCtl>(sv->sc), P<double>(h->powtab)};
+    ServeArgs a{sv->ring_dev, sv->slots, sv->idle_ns, P<ServeCtl>(sv->sc), P<double>(h->powtab), P<int2>(sv->ebuf)};
     void *args[] = {(void *)&g, (void *)&a};
     if (cudaLaunchCooperativeKernel((const void *)k_serve, dim3(h->num_sms * per_sm), dim3(threads), args, smem,
                                     sv->run) != cudaSuccess) {
@@ -1384,9 +1510,13 @@ static int server_service(plds_server *sv) {
     int32_t reset = kExitNone;
     cudaMemcpy(&reinterpret_cast<ServeCtl *>(sv->sc.p)->exit_reason, &reset, 4, cudaMemcpyHostToDevice);
     if (c.exit_reason == kExitNeedPool) {
+        const int64_t saved = h->pool_limit;
+        h->pool_limit = sv->pool_limit;
         int rc = grow_pool(h, (int64_t)c.grow_total);
+        h->pool_limit = saved;
         if (rc) return rc;
         cudaDeviceSynchronize();
+        sv->pool_used = h->pool_live;
     }
     if (sv->next_seq > c.head) return server_launch(sv);  // requests are waiting
     return PLDS_OK;
@@ -1406,7 +1536,13 @@ static void server_collect(plds_server *sv) {
         out.rounds = (int64_t)r->st[kStRounds];
         out.moves = (int64_t)r->st[kStMoves];
         out.device_ns = (int64_t)(r->t_end - r->t_begin);
+        out.batch_first = r->batch_first;
+        out.batch_size = r->batch_n;
+        out.done_ns = now_monotonic_ns();
         const int slot = (int)(sv->done_seq % sv->slots);
+        sv->pool_used = (int64_t)r->pool_top;
+        sv->inflight_need -= sv->need[slot];
+        sv->need[slot] = 0;
         if (r->op == kReqCoreness && sv->qdest[slot]) {
             std::memcpy(sv->qdest[slot], sv->qbuf, sizeof(double) * (size_t)sv->h->n);
             sv->qdest[slot] = nullptr;
@@ -1427,7 +1563,10 @@ static void server_free(plds_server *sv) {
     for (int32_t *p : sv->stage)
         if (p) cudaFreeHost(p);
     if (sv->qbuf) cudaFreeHost(sv->qbuf);
-    if (sv->h) dev_free(sv->h, sv->sc);
+    if (sv->h) {
+        dev_free(sv->h, sv->sc);
+        dev_free(sv->h, sv->ebuf);
+    }
     cudaGetLastError();
     delete sv;
 }
@@ -1451,6 +1590,7 @@ extern "C" plds_server_t *plds_server_create(plds_t *h, int32_t slots, int64_t m
     sv->max_batch = max_batch;
     cudaSetDevice(h->device);
     bool ok = ensure_batch_scratch(h, max_batch) && dev_get(h, sv->sc, sizeof(ServeCtl)) &&
+              dev_get(h, sv->ebuf, sizeof(int2) * (size_t)max_batch) &&
               cudaStreamCreateWithFlags(&sv->run, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&sv->done, cudaEventDisableTiming) == cudaSuccess &&
               cudaHostAlloc((void **)&sv->ring, sizeof(ReqSlot) * slots, cudaHostAllocMapped) == cudaSuccess &&
@@ -1462,11 +1602,10 @@ extern "C" plds_server_t *plds_server_create(plds_t *h, int32_t slots, int64_t m
         sv->stage.assign(slots, nullptr);
         sv->stage_dev.assign(slots, nullptr);
         sv->qdest.assign(slots, nullptr);
-        for (int i = 0; i < slots && ok; ++i) {
-            ok = cudaHostAlloc((void **)&sv->stage[i], sizeof(int32_t) * 2 * (size_t)max_batch, cudaHostAllocMapped) ==
-                     cudaSuccess &&
-                 cudaHostGetDevicePointer((void **)&sv->stage_dev[i], sv->stage[i], 0) == cudaSuccess;
-        }
+        sv->need.assign(slots, 0);
+        sv->merge_cap = max_batch;
+        sv->pool_used = h->pool_cap;  // unknown until the first completion: assume full
+        sv->stage_cap.assign(slots, 0);
     }
     if (ok) {
         ServeCtl c{};
@@ -1502,6 +1641,28 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
         if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(h->wait_limit_ns))
             return set_status(PLDS_ETIMEOUT);
     }
+    // admission: the adjacency must be able to grow to hold the batch (worst case)
+    const int64_t need = op == kReqInsert ? insert_need_slots(h, B) : 0;
+    for (;;) {
+        int64_t free_b = 0;
+        if (need > 0 && h->pool_cap - sv->pool_used - sv->inflight_need < need) {
+            size_t fb = 0, tb = 0;
+            if (cudaMemGetInfo(&fb, &tb) != cudaSuccess) {
+                cudaGetLastError();
+                fb = 0;
+            }
+            free_b = std::max<int64_t>(0, (int64_t)fb - kHbmReserve);
+            if (sv->pool_limit > 0) free_b = std::min<int64_t>(free_b, sv->pool_limit);
+        }
+        const int d = plds_server_admission(h->pool_cap, sv->pool_used, sv->inflight_need, need, free_b);
+        if (d == 0) break;
+        if (d != 1) return set_status(PLDS_ENOMEM);
+        server_collect(sv);
+        int rc = server_service(sv);
+        if (rc) return set_status(rc);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(h->wait_limit_ns))
+            return set_status(PLDS_ETIMEOUT);
+    }
     bool out_dev = false;
     void *out_devptr = nullptr;
     if (op == kReqCoreness) {
@@ -1524,6 +1685,7 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
     r->op = op;
     r->B = op == kReqCoreness ? 0 : B;
     r->ticket = sv->next_seq;
+    r->merge_cap = sv->merge_cap;
     r->edges = nullptr;
     r->out = nullptr;
     if (op != kReqCoreness && B > 0) {
@@ -1535,6 +1697,21 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
         if (dev) {
             r->edges = static_cast<const int32_t *>(pa.devicePointer);
         } else {  // pageable memory: copy into the slot's pinned staging
+            if (sv->stage_cap[slot] < B) {
+                if (sv->stage[slot]) cudaFreeHost(sv->stage[slot]);
+                sv->stage[slot] = nullptr;
+                sv->stage_cap[slot] = 0;
+                const int64_t cap = std::min<int64_t>(sv->max_batch, std::max<int64_t>(2 * B, 1 << 16));
+                if (cudaHostAlloc((void **)&sv->stage[slot], sizeof(int32_t) * 2 * (size_t)cap, cudaHostAllocMapped) !=
+                        cudaSuccess ||
+                    cudaHostGetDevicePointer((void **)&sv->stage_dev[slot], sv->stage[slot], 0) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (sv->stage[slot]) cudaFreeHost(sv->stage[slot]);
+                    sv->stage[slot] = nullptr;
+                    return set_status(PLDS_ENOMEM);
+                }
+                sv->stage_cap[slot] = cap;
+            }
             std::memcpy(sv->stage[slot], edges, sizeof(int32_t) * 2 * (size_t)B);
             r->edges = sv->stage_dev[slot];
         }
@@ -1543,6 +1720,8 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
         r->out = out_dev ? static_cast<double *>(out_devptr) : sv->qbuf_dev;
         sv->qdest[slot] = out_dev ? nullptr : out;
     }
+    sv->need[slot] = need;
+    sv->inflight_need += need;
     std::atomic_thread_fence(std::memory_order_release);
     *(volatile int32_t *)&r->state = kSlotReady;
     if (ticket) *ticket = sv->next_seq;
@@ -1554,6 +1733,23 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
         if (rc) return set_status(rc);
     }
     return set_status(PLDS_OK);
+}
+
+extern "C" int plds_server_configure(plds_server_t *sv, int64_t merge_max_edges, int64_t pool_limit_bytes) {
+    if (!sv || pool_limit_bytes < 0 || merge_max_edges < -1) return set_status(PLDS_EINVAL);
+    sv->merge_cap = merge_max_edges < 0 ? sv->max_batch : std::min(merge_max_edges, sv->max_batch);
+    sv->pool_limit = pool_limit_bytes;
+    return set_status(PLDS_OK);
+}
+
+extern "C" int plds_server_admission(int64_t pool_cap, int64_t pool_used, int64_t inflight, int64_t need,
+                                     int64_t free_bytes) {
+    if (pool_cap < 0 || pool_used < 0 || inflight < 0 || need < 0 || free_bytes < 0) return PLDS_EINVAL;
+    if (pool_cap - pool_used - inflight >= need) return 0;  // the pool has room
+    // otherwise the pool must grow: a compacting grow needs a new pool that holds
+    // every slot in use or promised, and it must fit in the free bytes
+    if ((pool_used + inflight + need) <= free_bytes / 4) return 0;
+    return inflight > 0 ? 1 : 2;
 }
 
 extern "C" int plds_server_poll(plds_server_t *sv, plds_request_result *out, int32_t cap) {

@@ -221,7 +221,7 @@ __device__ __forceinline__ int32_t next_pow2(int64_t x) {
     return c;
 }
 
-__device__ __forceinline__ int32_t sid_of(const GraphCtx &g, int32_t l) { return g.stamp_base + 1 + l; }
+__device__ __forceinline__ int32_t sid_of(int32_t stamp_base, int32_t l) { return stamp_base + 1 + l; }
 
 // A neighbour id read from a table; anything outside [0,n) other than the empty
 // and tombstone marks would be a corrupted slot, which is never dereferenced.
@@ -275,15 +275,15 @@ __device__ int block_exclusive(int x, int *sh32, int *total) {
 // (min,max), keeps one copy of each key (batch hash set), flags ids outside [0,n).
 // ---------------------------------------------------------------------------
 template <class Team>
-__device__ void step_canonicalise(Team &T, const GraphCtx &g) {
-    const int2 *e = reinterpret_cast<const int2 *>(g.edges);
+__device__ void step_canonicalise(Team &T, const GraphCtx &g, const BatchIn &in) {
+    const int2 *e = reinterpret_cast<const int2 *>(in.edges);
     unsigned long long loops = 0;
     const int64_t mask = g.hcap - 1;
-    for (int64_t i0 = (int64_t)T.wid() * 32; i0 < g.B; i0 += (int64_t)T.nwarps() * 32) {
+    for (int64_t i0 = (int64_t)T.wid() * 32; i0 < in.B; i0 += (int64_t)T.nwarps() * 32) {
         int64_t i = i0 + lane_id();
         bool fresh = false;
         unsigned long long key = 0;
-        if (i < g.B) {
+        if (i < in.B) {
             int2 uv = e[i];
             if (uv.x < 0 || uv.x >= g.n || uv.y < 0 || uv.y >= g.n) {
                 atomicOr(&g.ctl->err, kErrInvalidId);
@@ -311,9 +311,9 @@ __device__ void step_canonicalise(Team &T, const GraphCtx &g) {
 // collect the touched endpoints (deduplicated by stamp) and, for insertions, the
 // number of incoming edges per endpoint.
 template <class Team>
-__device__ void step_filter(Team &T, const GraphCtx &g) {
+__device__ void step_filter(Team &T, const GraphCtx &g, const BatchIn &in) {
     const int64_t U = (int64_t)g.ctl->ucount;
-    const int32_t stouch = g.stamp_base;
+    const int32_t stouch = in.stamp_base;
     unsigned long long filtered = 0;
     for (int64_t i0 = (int64_t)T.wid() * 32; i0 < U; i0 += (int64_t)T.nwarps() * 32) {
         int64_t i = i0 + lane_id();
@@ -325,7 +325,7 @@ __device__ void step_filter(Team &T, const GraphCtx &g) {
             u = (int32_t)(key >> 32);
             v = (int32_t)(key & 0xffffffffu);
             bool present = table_find(g.slots, g.off[u], g.cap[u], v);
-            keep = (g.op == kOpInsert) ? !present : present;
+            keep = (in.op == kOpInsert) ? !present : present;
             if (!keep) filtered++;
         }
         long long pos = warp_append64(&g.ctl->vcount, keep);
@@ -336,7 +336,7 @@ __device__ void step_filter(Team &T, const GraphCtx &g) {
         bool tv = keep && atomicExch(&g.stamp[v], stouch) != stouch;
         int pv = warp_append(&g.ctl->tcount, tv);
         if (tv) g.touched[pv] = v;
-        if (keep && g.op == kOpInsert) {
+        if (keep && in.op == kOpInsert) {
             atomicAdd(&g.inc[u], 1);
             atomicAdd(&g.inc[v], 1);
         }
@@ -901,7 +901,8 @@ __device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t
 }
 
 template <class Team>
-__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *wsm, RoundStage st) {
+__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base, const int32_t *sh_upmax, int32_t *wsm,
+                           RoundStage st) {
     unsigned long long visits = 0, scanned = 0;
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
@@ -929,7 +930,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             g.ctl->tlcnt[q] = 0;
             g.ctl->clcnt[q] = 0;
         }
-        const int32_t scur = sid_of(g, l), snext = sid_of(g, l + 1);
+        const int32_t scur = sid_of(stamp_base, l), snext = sid_of(stamp_base, l + 1);
         const int32_t cut = sh_upmax[l / g.Lg];
         st.f.gcnt = &g.ctl->fcnt[q];
         st.f.glist = g.F[q];
@@ -1335,7 +1336,7 @@ __device__ __forceinline__ int del_effect(const GraphCtx &g, int32_t w, int32_t 
 }
 
 template <class Team>
-__device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist,
+__device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base, const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist,
                            int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0, evals = 0, evisits = 0;
     const int lane = lane_id();
@@ -1348,7 +1349,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t *sh_dnmin, 
             if (T.leader()) report(g, kErrInternal, 7, l, r, 0);
             return false;
         }
-        const int32_t sid = sid_of(g, l);
+        const int32_t sid = sid_of(stamp_base, l);
         const uint64_t t_round = (g.trace && T.leader()) ? global_ns() : 0;
         st.pk.gcnt = &g.ctl->pcnt[q];
         st.pk.glist = g.P[q];
@@ -1548,7 +1549,7 @@ __device__ __forceinline__ void trace_steps(const GraphCtx &g, const uint64_t (&
 }
 
 template <class Team>
-__device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh, int stage_shift) {
+__device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t *sh, int stage_shift) {
     int32_t *sh_upmax = sh;
     int32_t *sh_dnmin = sh + kMaxGroups;
     int *sh_scan = sh + 2 * kMaxGroups;  // 64 ints
@@ -1572,15 +1573,15 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh, int stage_shi
         g.ctl->trace_n = 1;
         tmark[nmark++] = global_ns();
     }
-    if (g.B > 0) {
-        step_canonicalise(T, g);
+    if (in.B > 0) {
+        step_canonicalise(T, g, in);
         if (!T.sync()) return;  // ids outside [0,n): nothing has changed
         if (tr) tmark[nmark++] = global_ns();
-        step_filter(T, g);
+        step_filter(T, g, in);
         if (!T.sync()) return;
         if (tr) tmark[nmark++] = global_ns();
     }
-    if (g.op == kOpInsert) {
+    if (in.op == kOpInsert) {
         step_grow_request(T, g);
         if (!T.sync()) return;
         if (T.leader() && *g.pool_top + g.ctl->grow_total > (unsigned long long)g.pool_cap)
@@ -1603,7 +1604,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh, int stage_shi
             tmark[nmark++] = global_ns();
             trace_steps(g, tmark, nmark, -1);
         }
-        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
+        ins_rounds(T, g, in.stamp_base, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
     } else {
         if (T.leader()) {
             g.ctl->nextmin[0] = kInf;
@@ -1630,7 +1631,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, int32_t *sh, int stage_shi
             g.ctl->rcnt[1] = 0;
             g.ctl->rbcnt = 0;
         }
-        del_rounds(T, g, sh_dnmin, whist, sh_block, whist, stage_setup(sh_stage, stage_shift));
+        del_rounds(T, g, in.stamp_base, sh_dnmin, whist, sh_block, whist, stage_setup(sh_stage, stage_shift));
     }
 }
 

@@ -107,4 +107,14 @@ struct GraphCtx {
     Ctl *ctl;
 };
 
+// The per-batch inputs of one batch: kept apart from the graph's context so that a
+// loop applying many batches to one graph can keep that context in kernel
+// parameter space.
+struct BatchIn {
+    const int32_t *edges;  // int32[B][2]
+    int64_t B;
+    int32_t op;            // kOpInsert / kOpDelete
+    int32_t stamp_base;    // stamps of this batch are stamp_base + 1 .. stamp_base + K + 1
+};
+
 }  // namespace pl

@@ -52,7 +52,8 @@ class PldsTuning(ctypes.Structure):
 class RequestResult(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("op", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("valid", ctypes.c_int64), ("rounds", ctypes.c_int64), ("moves", ctypes.c_int64),
-                ("device_ns", ctypes.c_int64)]
+                ("device_ns", ctypes.c_int64), ("batch_first", ctypes.c_int64), ("batch_size", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("done_ns", ctypes.c_int64)]
 
 
 class PldsError(RuntimeError):
@@ -105,6 +106,8 @@ def load():
     L.plds_server_drain.argtypes = [vp]
     L.plds_server_destroy.argtypes = [vp]
     L.plds_server_destroy.restype = None
+    L.plds_server_configure.argtypes = [vp, i64, i64]
+    L.plds_server_admission.argtypes = [i64, i64, i64, i64, i64]
     L.plds_last_status.argtypes = []
     L.plds_destroy.argtypes = [vp]
     L.plds_destroy.restype = None
@@ -324,12 +327,22 @@ class Server:
     """Device-resident request loop over one PLDS graph (serving form)."""
     INSERT, DELETE, CORENESS = 0, 1, 2
 
-    def __init__(self, graph: "PLDS", slots: int = 8, max_batch: int = 1 << 20):
+    def __init__(self, graph: "PLDS", slots: int = 8, max_batch: int = 1 << 20, merge_max_edges: int = -1,
+                 pool_limit_bytes: int = 0):
+        """merge_max_edges: edges one merged batch may hold (0 = every request is its
+        own batch, -1 = max_batch); pool_limit_bytes: cap on the adjacency pool
+        (0 = free device memory only)."""
         self.g = graph
         self._sv = load().plds_server_create(graph._h, int(slots), int(max_batch))
         if not self._sv:
             raise PldsError(load().plds_last_status(), "plds_server_create")
         self._keep = {}  # buffers that must stay alive until their request finishes
+        self.configure(merge_max_edges, pool_limit_bytes)
+
+    def configure(self, merge_max_edges: int = -1, pool_limit_bytes: int = 0):
+        rc = load().plds_server_configure(self._sv, int(merge_max_edges), int(pool_limit_bytes))
+        if rc != PLDS_OK:
+            raise PldsError(rc, "plds_server_configure")
 
     def submit(self, op: int, edges=None, out=None) -> int:
         t = ctypes.c_int64()
@@ -354,7 +367,8 @@ class Server:
         if k < 0:
             raise PldsError(k, "plds_server_poll")
         res = [dict(ticket=r.ticket, op=r.op, status=r.status, valid=r.valid, rounds=r.rounds,
-                    moves=r.moves, device_ns=r.device_ns) for r in buf[:k]]
+                    moves=r.moves, device_ns=r.device_ns, batch_first=r.batch_first,
+                    batch_size=r.batch_size, done_ns=r.done_ns) for r in buf[:k]]
         for r in res:
             self._keep.pop(r["ticket"], None)
         return res
@@ -375,6 +389,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def server_admission(pool_cap: int, pool_used: int, inflight: int, need: int, free_bytes: int) -> int:
+    """The serving loop's admission rule (no device use): 0 admit, 1 wait, 2 reject."""
+    return load().plds_server_admission(int(pool_cap), int(pool_used), int(inflight), int(need),
+                                        int(free_bytes))
 
 
 def exported_symbols_in_header(header: os.PathLike | None = None):

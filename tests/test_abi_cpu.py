@@ -44,3 +44,19 @@ def test_invalid_parameters_rejected_without_device(lib):
         assert lib.plds_last_status() == P.PLDS_EINVAL
     assert lib.plds_batch_insert(None, None, 0) == P.PLDS_EINVAL
     assert lib.plds_levels(None, None) == P.PLDS_EINVAL
+
+
+def test_serving_admission_rule(lib):
+    """The serving loop's admission rule (pure host function): admit when the pool has
+    room or a grown pool holding every used and promised slot fits in free memory;
+    otherwise wait while earlier requests are in flight, else reject."""
+    A = P.server_admission
+    assert A(1000, 400, 100, 500, 0) == 0          # room in the pool, exactly
+    assert A(1000, 400, 0, 601, 0) == 2            # no room, nothing in flight, no memory
+    assert A(1000, 400, 101, 500, 0) == 1          # no room, but requests in flight
+    assert A(1000, 400, 100, 501, 4 * 1001) == 0   # a grown pool of 1001 slots fits
+    assert A(1000, 400, 100, 501, 4 * 1001 - 1) == 1
+    assert A(1000, 400, 0, 601, 4 * 1001 - 1) == 2
+    assert A(1000, 1000, 0, 0, 0) == 0             # deletions and queries need nothing
+    assert A(-1, 0, 0, 0, 0) == P.PLDS_EINVAL
+    assert A(0, 0, 0, 1, -5) == P.PLDS_EINVAL
