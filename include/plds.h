@@ -85,6 +85,8 @@ typedef struct plds_tuning {
                                  (exercises the bounded waits); 0 in normal use */
     int32_t trace_rounds;     /* diagnostics: 1 = record one line per level round (plds_trace) */
     int32_t barrier_sleep_ns; /* pause between polls of a grid-barrier wait (0 = default 32, -1 = none) */
+    int32_t block_cap;        /* tables above this many slots get a whole block for desire-levels
+                                 and rebuilds, smaller ones a warp (0 = default 4096, else >= 4) */
 } plds_tuning;
 
 /*
@@ -216,8 +218,37 @@ typedef struct plds_set plds_set_t;
 plds_set_t *plds_set_create(int32_t count, const int32_t *n, double delta, double lambda,
                             const plds_allocator *allocator, void *stream);
 int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_t *offsets);
+int plds_set_tune(plds_set_t *s, const plds_tuning *t);
+int plds_set_autotune(plds_set_t *s, int32_t rounds, const int32_t *const *edges, const int64_t *const *offsets,
+                      int32_t timed_from, int32_t max_trials, plds_tuning *best);
 plds_t *plds_set_graph(plds_set_t *s, int32_t i);
 void plds_set_destroy(plds_set_t *s);
+
+/*
+ * Autotuner (the paper has no counterpart: its cutoffs are a multicore design's).
+ * The knobs that change only speed -- the thread cutoff (thread_max_cap), the
+ * block cutoff (block_cap) and the hash load factor (load_num/load_den) -- are
+ * picked by coordinate descent: starting from `start`, each knob in that order
+ * takes every value of its candidate list with the others held, and keeps the
+ * value of lowest cost (a new value must cost at least 2 % less than the
+ * incumbent); passes repeat while one of them improves, within max_trials cost
+ * evaluations.  Candidates: thread_max_cap {4, 8, 16, 32, 64}, block_cap {1024,
+ * 2048, 4096, 8192, 16384}, load {1/2, 5/8, 3/4, 7/8}.
+ *   plds_tune_search: the search alone, against any cost function (no device use):
+ *     cost(t, ctx) returns a cost (seconds) or a negative value to stop the search
+ *     with PLDS_EINTERNAL.  *best gets the chosen knobs (the other fields of start
+ *     are kept); returns the number of evaluations or a negative code.
+ *   plds_set_tune: the same knobs for every graph of a set.
+ *   plds_set_autotune: the search for a set, on a sample of its workload: each
+ *     evaluation builds a scratch set of the same graph sizes, applies rounds
+ *     0..rounds-1 (edges[r], offsets[r] as for plds_set_update; rounds before
+ *     timed_from untimed, e.g. a preload) and costs the wall time of the rest.
+ *     The set itself is not changed except that the best knobs are applied to it
+ *     (and written to *best).
+ */
+typedef double (*plds_tune_cost)(const plds_tuning *t, void *ctx);
+int plds_tune_search(const plds_tuning *start, plds_tune_cost cost, void *ctx, int32_t max_trials,
+                     plds_tuning *best);
 
 /*
  * Serving form: a device-resident request loop over one graph (the paper has no

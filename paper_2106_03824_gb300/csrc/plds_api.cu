@@ -352,6 +352,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.thread_max_cap = h->tune.thread_max_cap > 0 ? h->tune.thread_max_cap : 16;
     g.load_num = h->tune.load_num > 0 ? h->tune.load_num : 3;
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
+    g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 4096;
     g.wait_limit_ns = h->wait_limit_ns;
     g.test_delay_us = h->tune.test_delay_us;
     g.barrier_sleep_ns = h->tune.barrier_sleep_ns == 0 ? 32 : (h->tune.barrier_sleep_ns < 0 ? 0 : h->tune.barrier_sleep_ns);
@@ -709,7 +710,7 @@ int plds_set_tuning(plds_t *h, const plds_tuning *t) {
         return set_status(PLDS_EINVAL);
     if (t->thread_max_cap < 0 || t->load_num < 0 || t->load_den < 0 || t->blocks_per_sm < 0 ||
         t->test_delay_us < 0 || t->test_delay_us > 10 * 1000 * 1000 || t->barrier_sleep_ns < -1 ||
-        t->barrier_sleep_ns > 100000)
+        t->barrier_sleep_ns > 100000 || t->block_cap < 0 || (t->block_cap > 0 && t->block_cap < 4))
         return set_status(PLDS_EINVAL);
     if ((t->load_num > 0) != (t->load_den > 0) || (t->load_num > 0 && (t->load_num * 8 > t->load_den * 7)))
         return set_status(PLDS_EINVAL);  // a table must keep an empty slot
@@ -916,9 +917,10 @@ __global__ void __launch_bounds__(kSetThreads, 2)
             int32_t *dst = reinterpret_cast<int32_t *>(&gsh);
             for (int k = threadIdx.x; k < (int)(sizeof(GraphCtx) / 4); k += blockDim.x) dst[k] = src[k];
             __syncthreads();
-            if (gsh.B == 0) continue;  // an empty half changes nothing
+            // the host reads both halves' control blocks: clear them even for an empty half
             int32_t *cw = reinterpret_cast<int32_t *>(gsh.ctl);
             for (int k = threadIdx.x; k < (int)(sizeof(Ctl) / 4); k += blockDim.x) cw[k] = 0;
+            if (gsh.B == 0) continue;  // an empty half changes nothing
             for (int64_t k = threadIdx.x; k < gsh.hcap; k += blockDim.x) gsh.hset[k] = kEmptyKey;
             if (gsh.op == kOpInsert)
                 for (int k = threadIdx.x; k <= gsh.K; k += blockDim.x) gsh.bins[k] = 0;
@@ -947,6 +949,11 @@ struct plds_set {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int32_t captured_count = -1;
+    // what plds_set_create was given (the autotuner builds scratch sets alike)
+    std::vector<int32_t> ns;
+    double delta = 0, lambda = 0;
+    plds_allocator alloc{};
+    bool has_alloc = false;
 };
 
 // Runs one round for n_items graphs on the private stream (the caller's stream
@@ -1003,6 +1010,13 @@ extern "C" plds_set_t *plds_set_create(int32_t count, const int32_t *n, double d
     }
     s->count = count;
     s->stream = (cudaStream_t)stream;
+    s->ns.assign(n, n + count);
+    s->delta = delta;
+    s->lambda = lambda;
+    if (allocator) {
+        s->alloc = *allocator;
+        s->has_alloc = true;
+    }
     for (int32_t i = 0; i < count; ++i) {
         plds_t *h = plds_create_ex(n[i], delta, lambda, 0, allocator, stream, 0);
         if (!h) {
@@ -1089,7 +1103,6 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
                     h->stamp_base = 1;
                 }
                 GraphCtx g = make_ctx(h, half == 0 ? kOpInsert : kOpDelete, dedges + 2 * offsets[2 * gi + half], b);
-                g.thread_max_cap = std::min(g.thread_max_cap, 16);
                 g.ctl = dctl + 2 * j + half;
                 g.trace = nullptr;
                 g.trace_cap = 0;
@@ -1110,7 +1123,8 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
             const int32_t gi = todo[j];
             plds *h = s->g[gi];
             const Ctl &ci = s->h_ctls[2 * j], &cd = s->h_ctls[2 * j + 1];
-            const int32_t err = ci.err | cd.err;
+            // the deletion half runs only after a clean insertion half
+            const int32_t err = ci.err ? ci.err : cd.err;
             if (err & kErrInvalidId) return set_status(PLDS_EINVAL);
             if (err == kErrNeedPool) {
                 int rc = grow_pool(h, (int64_t)ci.grow_total);
@@ -1142,6 +1156,149 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
         todo.swap(again);
     }
     return set_status(todo.empty() ? PLDS_OK : PLDS_ENOMEM);
+}
+
+extern "C" int plds_set_tune(plds_set_t *s, const plds_tuning *t) {
+    if (!s || !t) return set_status(PLDS_EINVAL);
+    for (plds *h : s->g) {
+        plds_tuning x = h->tune;
+        x.thread_max_cap = t->thread_max_cap;
+        x.block_cap = t->block_cap;
+        x.load_num = t->load_num;
+        x.load_den = t->load_den;
+        const int rc = plds_set_tuning(h, &x);
+        if (rc) return rc;
+    }
+    return set_status(PLDS_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: coordinate descent over the knobs that change only speed.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int32_t kTuneThread[] = {4, 8, 16, 32, 64};
+constexpr int32_t kTuneBlock[] = {1024, 2048, 4096, 8192, 16384};
+constexpr int32_t kTuneLoad[][2] = {{1, 2}, {5, 8}, {3, 4}, {7, 8}};
+
+bool same_knobs(const plds_tuning &a, const plds_tuning &b) {
+    return a.thread_max_cap == b.thread_max_cap && a.block_cap == b.block_cap && a.load_num == b.load_num &&
+           a.load_den == b.load_den;
+}
+
+struct SetTuneCtx {
+    plds_set *s;
+    int32_t rounds;
+    const int32_t *const *edges;
+    const int64_t *const *offsets;
+    int32_t timed_from;
+    int status;
+};
+
+// One evaluation: a scratch set of the same graph sizes, the sample rounds, the
+// wall time of the timed ones (every plds_set_update call returns when done).
+double set_trial_cost(const plds_tuning *t, void *vctx) {
+    SetTuneCtx *c = static_cast<SetTuneCtx *>(vctx);
+    plds_set *s = c->s;
+    plds_set_t *x = plds_set_create(s->count, s->ns.data(), s->delta, s->lambda, s->has_alloc ? &s->alloc : nullptr,
+                                    (void *)s->stream);
+    if (!x) {
+        c->status = plds_last_status();
+        return -1.0;
+    }
+    int rc = plds_set_tune(x, t);
+    double secs = 0.0;
+    for (int32_t r = 0; r < c->rounds && rc == PLDS_OK; ++r) {
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = plds_set_update(x, c->edges[r], c->offsets[r]);
+        if (r >= c->timed_from) secs += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    plds_set_destroy(x);
+    if (rc != PLDS_OK) {
+        c->status = rc;
+        return -1.0;
+    }
+    return secs;
+}
+}  // namespace
+
+extern "C" int plds_tune_search(const plds_tuning *start, plds_tune_cost cost, void *ctx, int32_t max_trials,
+                                plds_tuning *best) {
+    if (!start || !cost || !best || max_trials < 1) return set_status(PLDS_EINVAL);
+    plds_tuning cur = *start;
+    if (cur.thread_max_cap <= 0) cur.thread_max_cap = 16;
+    if (cur.block_cap <= 0) cur.block_cap = 4096;
+    if (cur.load_num <= 0 || cur.load_den <= 0) {
+        cur.load_num = 3;
+        cur.load_den = 4;
+    }
+    std::vector<std::pair<plds_tuning, double>> seen;  // every evaluation, to skip repeats
+    int32_t trials = 0;
+    // 0: cost in *c; 1: budget spent; -1: the cost function gave up
+    auto eval = [&](const plds_tuning &t, double *c) -> int {
+        for (const auto &e : seen)
+            if (same_knobs(e.first, t)) {
+                *c = e.second;
+                return 0;
+            }
+        if (trials >= max_trials) return 1;
+        const double v = cost(&t, ctx);
+        ++trials;
+        if (!(v >= 0.0)) return -1;
+        seen.push_back({t, v});
+        *c = v;
+        return 0;
+    };
+    double cur_cost = 0.0;
+    if (eval(cur, &cur_cost) < 0) return set_status(PLDS_EINTERNAL);
+    bool improved = true, spent = false;
+    while (improved && !spent) {
+        improved = false;
+        for (int knob = 0; knob < 3 && !spent; ++knob) {
+            const int nv = knob == 2 ? 4 : 5;
+            for (int v = 0; v < nv; ++v) {
+                plds_tuning t = cur;
+                if (knob == 0) {
+                    t.thread_max_cap = kTuneThread[v];
+                } else if (knob == 1) {
+                    t.block_cap = kTuneBlock[v];
+                } else {
+                    t.load_num = kTuneLoad[v][0];
+                    t.load_den = kTuneLoad[v][1];
+                }
+                if (same_knobs(t, cur)) continue;
+                double c = 0.0;
+                const int rc = eval(t, &c);
+                if (rc < 0) return set_status(PLDS_EINTERNAL);
+                if (rc > 0) {
+                    spent = true;
+                    break;
+                }
+                if (c < 0.98 * cur_cost) {
+                    cur = t;
+                    cur_cost = c;
+                    improved = true;
+                }
+            }
+        }
+    }
+    *best = cur;
+    set_status(PLDS_OK);
+    return trials;
+}
+
+extern "C" int plds_set_autotune(plds_set_t *s, int32_t rounds, const int32_t *const *edges,
+                                 const int64_t *const *offsets, int32_t timed_from, int32_t max_trials,
+                                 plds_tuning *best) {
+    if (!s || rounds < 1 || !edges || !offsets || timed_from < 0 || timed_from >= rounds || max_trials < 1)
+        return set_status(PLDS_EINVAL);
+    SetTuneCtx c{s, rounds, edges, offsets, timed_from, PLDS_OK};
+    plds_tuning out{};
+    const int trials = plds_tune_search(&s->g[0]->tune, set_trial_cost, &c, max_trials, &out);
+    if (trials < 0) return set_status(c.status != PLDS_OK ? c.status : trials);
+    const int rc = plds_set_tune(s, &out);
+    if (rc) return rc;
+    if (best) *best = out;
+    return set_status(PLDS_OK);
 }
 
 extern "C" void plds_set_destroy(plds_set_t *s) {

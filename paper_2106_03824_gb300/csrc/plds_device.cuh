@@ -369,8 +369,6 @@ __device__ void step_grow_request(Team &T, const GraphCtx &g) {
     }
 }
 
-constexpr int32_t kBigTable = 4096;  // tables above this many slots are rebuilt by a block or the team
-
 // Second pass (after the pool check): allocate and rehash.  Small tables: one
 // warp each.  Large tables (hubs): one block each, so a hub's rebuild is not
 // left to a single warp.
@@ -382,7 +380,7 @@ __device__ bool step_grow_apply(Team &T, const GraphCtx &g) {
         const unsigned long long noff = atomicAdd(g.pool_top, (unsigned long long)it.y);
         const int4 rec = make_int4(it.x, it.y, (int32_t)(noff & 0xffffffffu), (int32_t)(noff >> 32));
         g.M[0][i] = rec;
-        if (it.y > kBigTable) {
+        if (it.y > g.block_cap) {
             const int b = atomicAdd(&g.ctl->mcnt[1], 1);
             g.M[1][b] = rec;
         }
@@ -391,7 +389,7 @@ __device__ bool step_grow_apply(Team &T, const GraphCtx &g) {
     for (int i = T.wid(); i < gc; i += T.nwarps()) {
         const int4 it = g.M[0][i];
         const int32_t x = it.x, nc = it.y;
-        if (nc > kBigTable) continue;
+        if (nc > g.block_cap) continue;
         const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
         int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
         for (int j = lane_id(); j < (nc >> 2); j += 32) nt[j] = empty4();
@@ -508,7 +506,7 @@ __device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
             base = atomicAdd(&g.ctl->shrink_used, d);
             if ((int64_t)base + d > g.arena_cap) want = false;
         }
-        const bool big = want && c > kBigTable;
+        const bool big = want && c > g.block_cap;
         if (big) {  // a whole block rebuilds it below
             const int b = atomicAdd(&g.ctl->mcnt[1], 1);
             g.M[1][b] = make_int4(x, nc, base, d);
@@ -1248,8 +1246,6 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     }
 }
 
-constexpr int32_t kBlockDlCap = 4096;  // tables larger than this get a block per desire-level
-
 // Desire-levels for every vertex of src[0..count) that violates Invariant 2
 // (level > 0 and up* < dnmin[gn(level-1)]).  Two phases with a team barrier:
 // classify into a warp list (small tables, from the front of RL) and a block list
@@ -1270,7 +1266,7 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
             w = src[i];
             const int32_t lw = g.level[w], us = g.upstar[w], c = g.cap[w];
             viol = lw > 0 && us < sh_dnmin[(lw - 1) / g.Lg];
-            big = c > kBlockDlCap;
+            big = c > g.block_cap;
         }
         const int pw = warp_append(&g.ctl->rcnt[1], viol && !big);
         if (viol && !big) RL[pw] = w;

@@ -68,7 +68,7 @@ struct GraphCtx {
     int32_t load_num, load_den;
     int32_t test_delay_us;
     int32_t barrier_sleep_ns;
-    int32_t pad1;
+    int32_t block_cap;     // tables above this many slots get a whole block (desire-levels, rebuilds)
     int64_t wait_limit_ns;
     const int32_t *upmax;  // [G]
     const int32_t *dnmin;  // [G]

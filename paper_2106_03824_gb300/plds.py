@@ -46,7 +46,16 @@ class PldsTuning(ctypes.Structure):
     _fields_ = [("thread_max_cap", ctypes.c_int32), ("load_num", ctypes.c_int32),
                 ("load_den", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("test_delay_us", ctypes.c_int32),
-                ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32)]
+                ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32),
+                ("block_cap", ctypes.c_int32)]
+
+    KNOBS = ("thread_max_cap", "block_cap", "load_num", "load_den")
+
+    def knobs(self) -> dict:
+        return {k: int(getattr(self, k)) for k in self.KNOBS}
+
+
+TUNE_COST = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(PldsTuning), ctypes.c_void_p)
 
 
 class RequestResult(ctypes.Structure):
@@ -99,6 +108,10 @@ def load():
     L.plds_set_graph.argtypes = [vp, i32]
     L.plds_set_destroy.argtypes = [vp]
     L.plds_set_destroy.restype = None
+    L.plds_set_tune.argtypes = [vp, ctypes.POINTER(PldsTuning)]
+    L.plds_set_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                    i32, i32, ctypes.POINTER(PldsTuning)]
+    L.plds_tune_search.argtypes = [ctypes.POINTER(PldsTuning), TUNE_COST, vp, i32, ctypes.POINTER(PldsTuning)]
     L.plds_server_create.restype = vp
     L.plds_server_create.argtypes = [vp, i32, i64]
     L.plds_server_submit.argtypes = [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_int64)]
@@ -296,6 +309,36 @@ class PLDSSet:
             raise PldsError(rc, "plds_set_update")
         return rc
 
+    def tune(self, **knobs):
+        """Apply thread_max_cap / block_cap / load_num / load_den to every graph."""
+        t = PldsTuning()
+        for k, v in knobs.items():
+            setattr(t, k, int(v))
+        rc = load().plds_set_tune(self._s, ctypes.byref(t))
+        if rc != PLDS_OK:
+            raise PldsError(rc, "plds_set_tune")
+
+    def autotune(self, rounds, timed_from: int = 0, max_trials: int = 24) -> dict:
+        """Pick the knobs on a sample of the workload: rounds = [(edges, offsets)]
+        (as for update; device tensors give representative timings), the ones before
+        timed_from untimed.  Applies the best knobs and returns them."""
+        keep = []
+        ep = (ctypes.c_void_p * len(rounds))()
+        op = (ctypes.c_void_p * len(rounds))()
+        for r, (e, o) in enumerate(rounds):
+            if isinstance(e, np.ndarray):
+                e = np.ascontiguousarray(e, dtype=np.int32).reshape(-1, 2)
+            o = np.ascontiguousarray(o, dtype=np.int64)
+            keep.append((e, o))
+            ep[r] = _ptr(e).value
+            op[r] = _ptr(o).value
+        best = PldsTuning()
+        rc = load().plds_set_autotune(self._s, len(rounds), ep, op, int(timed_from), int(max_trials),
+                                      ctypes.byref(best))
+        if rc != PLDS_OK:
+            raise PldsError(rc, "plds_set_autotune")
+        return best.knobs()
+
     @staticmethod
     def pack(halves):
         """[(ins_i, del_i)] per graph -> (edges [total,2], offsets [2*count+1])."""
@@ -389,6 +432,27 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_search(cost, start: dict | None = None, max_trials: int = 24):
+    """The autotuner's coordinate descent against a Python cost function
+    cost(knobs: dict) -> float (no device use).  Returns (best knobs, evaluations)."""
+    st = PldsTuning()
+    for k, v in (start or {}).items():
+        setattr(st, k, int(v))
+
+    def _cb(t, _ctx):
+        try:
+            return float(cost(t.contents.knobs()))
+        except Exception:
+            return -1.0
+
+    cb = TUNE_COST(_cb)
+    best = PldsTuning()
+    k = load().plds_tune_search(ctypes.byref(st), cb, None, int(max_trials), ctypes.byref(best))
+    if k < 0:
+        raise PldsError(k, "plds_tune_search")
+    return best.knobs(), k
 
 
 def server_admission(pool_cap: int, pool_used: int, inflight: int, need: int, free_bytes: int) -> int:

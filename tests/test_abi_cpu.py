@@ -60,3 +60,36 @@ def test_serving_admission_rule(lib):
     assert A(1000, 1000, 0, 0, 0) == 0             # deletions and queries need nothing
     assert A(-1, 0, 0, 0, 0) == P.PLDS_EINVAL
     assert A(0, 0, 0, 1, -5) == P.PLDS_EINVAL
+
+
+def test_tune_search_finds_the_minimum_of_a_separable_cost(lib):
+    """Coordinate descent over (thread cutoff, block cutoff, load factor) against a
+    fake cost with its minimum at (8, 8192, 5/8): found from the defaults, every
+    evaluation inside the candidate lists, no configuration evaluated twice."""
+    import math
+    seen = []
+
+    def cost(k):
+        seen.append(tuple(k.values()))
+        return (1.0 + (math.log2(k["thread_max_cap"]) - 3) ** 2 + 0.5 * (math.log2(k["block_cap"]) - 13) ** 2
+                + 10 * abs(k["load_num"] / k["load_den"] - 0.625))
+
+    best, n = P.tune_search(cost)
+    assert best == {"thread_max_cap": 8, "block_cap": 8192, "load_num": 5, "load_den": 8}
+    assert n == len(seen) == len(set(seen))
+    for t, b, ln, ld in seen:
+        assert t in (4, 8, 16, 32, 64) and b in (1024, 2048, 4096, 8192, 16384)
+        assert (ln, ld) in ((1, 2), (5, 8), (3, 4), (7, 8))
+
+
+def test_tune_search_budget_and_failure(lib):
+    calls = []
+    best, n = P.tune_search(lambda k: calls.append(k) or 1.0, max_trials=3)
+    assert n == 3 and len(calls) == 3
+    assert best == {"thread_max_cap": 16, "block_cap": 4096, "load_num": 3, "load_den": 4}  # flat: defaults kept
+    with pytest.raises(P.PldsError) as ex:
+        P.tune_search(lambda k: -1.0)
+    assert ex.value.code == P.PLDS_EINTERNAL
+    # a 1 % gain is below the 2 % threshold: the incumbent stays
+    best, _ = P.tune_search(lambda k: 0.99 if k["thread_max_cap"] == 4 else 1.0)
+    assert best["thread_max_cap"] == 16

@@ -93,3 +93,44 @@ def test_set_rejects_bad_ids(P):
     edges, offs = S.pack(halves)
     assert S.update(edges, offs, check=False) == P.PLDS_EINVAL
     S.close()
+
+
+def test_set_knobs_never_change_results_and_autotune(P):
+    """Thread cutoff, block cutoff and load factor change only speed: a set under
+    extreme knobs (and under the knobs the autotuner picks on a sample of the same
+    workload) ends every round with the same levels as the default set."""
+    graphs = _graphs(24, seed=8)
+    ns = [n for n, _ in graphs]
+    rng = np.random.default_rng(4)
+    present = [set() for _ in graphs]
+    rounds = []
+    for r in range(5):
+        halves = [_round(rng, e, present[i], n, 100 * r + i) for i, (n, e) in enumerate(graphs)]
+        for i, (ins, dele) in enumerate(halves):
+            for u, v in ins:
+                if u != v:
+                    present[i].add((min(u, v), max(u, v)))
+            for u, v in dele:
+                present[i].discard((min(u, v), max(u, v)))
+        rounds.append(P.PLDSSet.pack(halves))
+    dev = [(torch.from_numpy(e).cuda(), o) for e, o in rounds]
+    ref = P.PLDSSet(ns)
+    want = []
+    for e, o in dev:
+        ref.update(e, o)
+        want.append([g.levels().copy() for g in ref.graphs])
+    ref.close()
+    tuned = P.PLDSSet(ns)
+    best = tuned.autotune(dev[:3], timed_from=1, max_trials=8)
+    assert best["thread_max_cap"] in (4, 8, 16, 32, 64)
+    assert best["block_cap"] in (1024, 2048, 4096, 8192, 16384)
+    assert (best["load_num"], best["load_den"]) in ((1, 2), (5, 8), (3, 4), (7, 8))
+    extreme = P.PLDSSet(ns)
+    extreme.tune(thread_max_cap=4, block_cap=4, load_num=1, load_den=2)
+    for r, (e, o) in enumerate(dev):
+        for S in (tuned, extreme):
+            S.update(e, o)
+            for i, g in enumerate(S.graphs):
+                assert np.array_equal(g.levels(), want[r][i]), (r, i, best)
+    tuned.close()
+    extreme.close()
