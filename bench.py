@@ -209,21 +209,40 @@ def run_batched(args):
     from paper_2106_03824_gb300 import plds as P
     torch.cuda.set_device(0)
     ns, pre, rnds = make_batched(args.graphs, args.rounds)
-    S = P.PLDSSet(ns)
-    e0, o0 = S.pack([(p_, np.zeros((0, 2), np.int32)) for p_ in pre])
-    S.update(torch.from_numpy(e0).cuda(), o0)
-    packed = [S.pack(r) for r in rnds]
+    e0, o0 = P.PLDSSet.pack([(p_, np.zeros((0, 2), np.int32)) for p_ in pre])
+    pre_dev = (torch.from_numpy(e0).cuda(), o0)
+    packed = [P.PLDSSet.pack(r) for r in rnds]
     dev = [(torch.from_numpy(e).cuda(), o) for e, o in packed]
     upd = [int(o[-1]) for _, o in packed]
     w = min(args.warmup, args.rounds - 1)
-    for r in range(w):
-        S.update(*dev[r])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in range(w, args.rounds):
-        S.update(*dev[r])
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+
+    def timed_set(tuning):
+        """Preload, warm-up rounds, then the timed rounds; returns (seconds, set)."""
+        S = P.PLDSSet(ns)
+        if tuning:
+            S.tune(**tuning)
+        S.update(*pre_dev)
+        for r in range(w):
+            S.update(*dev[r])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(w, args.rounds):
+            S.update(*dev[r])
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, S
+
+    # knobs picked by the autotuner on the preload and warm-up rounds only
+    tuning = None
+    t_tune = 0.0
+    if not args.no_autotune and w > 0:
+        probe = P.PLDSSet(ns)
+        t0 = time.perf_counter()
+        tuning = probe.autotune([pre_dev] + dev[:w], timed_from=1, max_trials=args.tune_trials)
+        t_tune = time.perf_counter() - t0
+        probe.close()
+    dt_default, S0 = timed_set(None)
+    S0.close()
+    dt, S = timed_set(tuning)
     lat = dt / (args.rounds - w)
     batched = sum(upd[w:]) / dt
     # the plain form: one synchronous insert and delete call per graph, graphs one after another
@@ -256,7 +275,10 @@ def run_batched(args):
                        "total_vertices": int(sum(ns)), "updates_per_round": int(np.mean(upd))},
             "plain_loop": {"value": plain, "unit": UNIT, "rounds_timed": nplain,
                            "ms_per_round": 1e3 * dtp / nplain},
-            "speedup_vs_plain": batched / plain, "levels_equal_plain": same}
+            "speedup_vs_plain": batched / plain, "levels_equal_plain": same,
+            "autotune": {"knobs": tuning, "seconds": t_tune, "trials_max": args.tune_trials,
+                         "sample": "preload + warm-up rounds (untimed)",
+                         "default_knobs_updates_per_s": sum(upd[w:]) / dt_default}}
     print(json.dumps(line), flush=True)
 
 
@@ -429,6 +451,8 @@ def main():
     ap.add_argument("--graphs", type=int, default=512)
     ap.add_argument("--rounds", type=int, default=20)
     ap.add_argument("--plain-rounds", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-trials", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
