@@ -43,7 +43,7 @@ UNIT = "updates/s"
 # dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": None, "dram_per_algo_byte": None, "capture": None}
+NCU_TRAFFIC = {"kernel_sha": "e3bf78f05dd9ed62", "dram_per_algo_byte": 0.10744, "capture": "profiles/k_batch_grid_traffic_rmat20_B1e6.md"}
 
 
 def kernel_sha() -> str:
@@ -417,7 +417,11 @@ def run_serving(args):
                 **({"device_batches": len(sizes), "max_requests_per_batch": int(max(sizes))} if sizes else {})}
     best = results["served@90%"]
     line = {"metric": "edge updates/s and p50/p99 batch latency, serving form (device-resident request loop)",
-            "value": best["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 0,
+            "value": results["served_capacity_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
+            "warmup": 0, "p50_ms_at_90pct": best["p50_ms"], "p99_ms_at_90pct": best["p99_ms"],
+            "plain": {"capacity_updates_per_s": results["plain_capacity_updates_per_s"],
+                      "p50_ms_at_90pct": results["plain@90%"]["p50_ms"],
+                      "p99_ms_at_90pct": results["plain@90%"]["p99_ms"]},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "form": "serving",
             "config": {"workload": f"Chung-Lu n={n}, m={e.shape[0]}, exponent 2.2, 90% preloaded; "
@@ -443,6 +447,7 @@ def main():
     ap.add_argument("--cpu-batch", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dump-recs", default=None, help="write per-step kernel records (JSON) to this path")
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
     ap.add_argument("--serve-n", type=int, default=4_800_000)
     ap.add_argument("--serve-m", type=int, default=43_000_000)
@@ -530,6 +535,10 @@ def main():
     traffic = None
     if NCU_TRAFFIC["kernel_sha"] == kernel_sha() and NCU_TRAFFIC["dram_per_algo_byte"]:
         traffic = NCU_TRAFFIC["dram_per_algo_byte"] * abytes / len(recs)
+    if args.dump_recs:  # per timed step: the batch kernel's algorithmic bytes (matches ncu launch lists)
+        with open(args.dump_recs, "w") as f:
+            json.dump([{"algo_bytes": algo_bytes(r), "kernel_ns": r["kernel_ns"], "launches": r["launches"],
+                        "valid": r["valid"]} for r in recs], f)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": "k_batch_grid", "peak_source": peak_src,
