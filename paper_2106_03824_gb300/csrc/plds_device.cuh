@@ -44,30 +44,35 @@ struct GridTeam {
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
     // Grid-wide barrier with a bounded wait: a block that waits longer than
     // limit_ns (or sees the error word set) records kErrTimeout and leaves.
+    // One 64-bit arrival counter, never reset: the k-th barrier is passed once
+    // the counter reaches (k+1) x blocks.  Thread 0 of each block arrives with a
+    // release add and polls with acquire loads; the block barriers around it
+    // carry the other threads' writes and reads.
     __device__ bool sync() {
         __syncthreads();
         if (threadIdx.x == 0) {
-            volatile unsigned *genp = &ctl->bar_gen;
+            unsigned long long *cnt = &ctl->bar_arrivals;
+            unsigned long long a;
+            asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(a) : "l"(cnt) : "memory");
+            const unsigned long long target = (a / gridDim.x + 1) * (unsigned long long)gridDim.x;
             volatile int32_t *errp = &ctl->err;
-            unsigned gen = *genp;
-            __threadfence();
-            unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&ctl->bar_count, 0u);
-                __threadfence();
-                atomicAdd(&ctl->bar_gen, 1u);
-            } else {
-                uint64_t t0 = global_ns();
-                unsigned spins = 0;
-                while (*genp == gen && *errp == 0) {
-                    if ((++spins & 63u) == 0 && global_ns() - t0 > (uint64_t)limit_ns) {
+            uint64_t t0 = 0;
+            unsigned spins = 0;
+            for (;;) {
+                unsigned long long v;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(cnt) : "memory");
+                if (v >= target || *errp != 0) break;
+                if ((++spins & 63u) == 0) {
+                    const uint64_t now = global_ns();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > (uint64_t)limit_ns) {
                         atomicOr(&ctl->err, kErrTimeout);
                         break;
                     }
-                    if (sleep_ns) __nanosleep(sleep_ns);
                 }
+                if (sleep_ns) __nanosleep(sleep_ns);
             }
-            __threadfence();
         }
         __syncthreads();
         return ld_volatile(&ctl->err) == 0;

@@ -33,8 +33,7 @@ enum : int32_t { kOpInsert = 0, kOpDelete = 1 };
 
 // Control words of one graph, in device memory.
 struct Ctl {
-    unsigned bar_count;   // grid barrier arrivals
-    unsigned bar_gen;     // grid barrier generation
+    unsigned long long bar_arrivals;  // grid barrier: arrivals since launch (never reset within one)
     int32_t err;          // kErr* bits
     int32_t rounds_done;  // loop guard
     unsigned long long ucount;   // unique canonical keys
