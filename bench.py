@@ -125,6 +125,53 @@ def make_stream(scale: int, batch: int, seed: int = 1):
     return e, ins, dele, steps
 
 
+def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3):
+    """The experiments' Ins / Del / Mix protocols on the same graph, plain form,
+    device-resident inputs: Ins all edges from empty and Del them all, in batches of
+    1e6 and 1e5; Mix = 50/50 insert/delete batches of 1e6 on a 90 %-loaded graph
+    (untimed preload).  Per protocol: updates/s over the whole sequence and the
+    p50/p99 of the per-batch latency, both from CUDA events on the handle's stream."""
+    import torch
+
+    def timed(g, calls):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+        upd = 0
+        torch.cuda.synchronize()
+        evs[0].record()
+        for i, (fn, b) in enumerate(calls):
+            fn(b)
+            upd += b.shape[0]
+            evs[i + 1].record()
+        torch.cuda.synchronize()
+        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(calls))]
+        tot = evs[0].elapsed_time(evs[-1])
+        return {"updates_per_s": upd / (tot / 1e3), "batches": len(calls),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    out = {}
+    for B in (1_000_000, 100_000):
+        tag = "1e6" if B == 1_000_000 else "1e5"
+        g = P.PLDS(n)
+        out[f"ins_{tag}"] = timed(g, [(g.insert, ins_d[s:s + B]) for s in range(0, ins_d.shape[0], B)])
+        out[f"del_{tag}"] = timed(g, [(g.delete, del_d[s:s + B]) for s in range(0, del_d.shape[0], B)])
+        g.close()
+    pre, mixes = W.mix_stream(e, 1_000_000, mix_batches, load=0.9, seed=seed)
+    g = P.PLDS(n)
+    pre_d = torch.from_numpy(pre).cuda()
+    for s in range(0, pre_d.shape[0], 1_000_000):
+        g.insert(pre_d[s:s + 1_000_000])
+    calls = []
+    for a, b in mixes:  # a mixed batch: its insertion half, then its deletion half
+        calls.append((g.insert, torch.from_numpy(a).cuda()))
+        calls.append((g.delete, torch.from_numpy(b).cuda()))
+    m = timed(g, calls)
+    g.close()
+    m["batches"] = len(mixes)
+    m["note"] = "p50/p99 over the halves (each half is one call)"
+    out["mix_1e6"] = m
+    return out
+
+
 def cpu_sample(scale, ins, sample_batch=500_000):
     """The oracle (as it stands, 1 core) on a bounded prefix of the stream's first batch."""
     from oracle import oracle as O
@@ -447,6 +494,7 @@ def main():
     ap.add_argument("--cpu-batch", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-protocols", action="store_true")
     ap.add_argument("--dump-recs", default=None, help="write per-step kernel records (JSON) to this path")
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
     ap.add_argument("--serve-n", type=int, default=4_800_000)
@@ -569,6 +617,12 @@ def main():
         e2e = {"value": upd2 * world / dt2, "unit": UNIT, "h2d_bytes_per_step": 8 * upd2 / args.steps,
                "d2h_bytes_per_step": 8 * n}
 
+    # per-batch latency of the timed steps (kernel time of each call)
+    lat_ms = [r["kernel_ns"] / 1e6 for r in recs]
+    protocols = None
+    if world == 1 and not args.no_protocols:
+        protocols = run_protocols(P, n, e, ins_d, del_d)
+
     phases = {}
     for kind in ("ins", "del"):
         sel = [(r, steps[(args.warmup + i) % len(steps)]) for i, r in enumerate(recs)
@@ -601,6 +655,9 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "phases": phases,
+        "batch_latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                             "of": "batch kernel time of each timed step"},
+        "protocols": protocols,
     }
     print(json.dumps(line), flush=True)
     if dist:
