@@ -150,7 +150,7 @@ struct plds {
     int64_t pool_live = 0;   // slots in use after the last compaction
     int64_t pool_limit = 0;  // bytes a grown pool may take (0: free HBM only)
     // scratch: n-sized
-    DevBuf F[2], M[2], TL[2], P[2], R, R2, bins, levlist, CL[2];
+    DevBuf acc, M[2], TL[3], P[2], R, R2, bins, levlist, CL[3];
     int64_t clcap = 0;
     // scratch: batch-sized
     DevBuf edges, hset, ukeys, vkeys, touched, S, arena, trace;
@@ -221,16 +221,16 @@ static int64_t pow2_at_least(int64_t x) {
 static void free_all(plds *h) {
     DevBuf *bufs[] = {&h->upmax, &h->dnmin, &h->powtab, &h->level, &h->deg,   &h->up,    &h->upstar,
                       &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->inc,   &h->pool,
-                      &h->pool_top, &h->ctl, &h->F[0],  &h->F[1],  &h->M[0],  &h->M[1],  &h->TL[0],
-                      &h->TL[1], &h->P[0],  &h->P[1],   &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0],
-                      &h->CL[1], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace};
+                      &h->pool_top, &h->ctl, &h->acc,   &h->M[0],  &h->M[1],  &h->TL[0], &h->TL[1], &h->TL[2],
+                      &h->P[0],  &h->P[1],  &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0], &h->CL[1],
+                      &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace};
     for (DevBuf *b : bufs) dev_free(h, *b);
 }
 
 static bool alloc_chunk_lists(plds *h) {
     int64_t need = h->pool_cap / kChunk + (int64_t)h->n + 1024;
     if (h->clcap >= need) return true;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (!dev_get(h, h->CL[i], sizeof(int4) * (size_t)need)) return false;
     h->clcap = need;
     return true;
@@ -382,12 +382,14 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.bins = P<int32_t>(h->bins);
     g.levlist = P<int32_t>(h->levlist);
     for (int i = 0; i < 2; ++i) {
-        g.F[i] = P<int32_t>(h->F[i]);
         g.M[i] = P<int4>(h->M[i]);
-        g.TL[i] = P<int4>(h->TL[i]);
-        g.CL[i] = P<int4>(h->CL[i]);
         g.P[i] = P<int4>(h->P[i]);
     }
+    for (int i = 0; i < 3; ++i) {
+        g.TL[i] = P<int4>(h->TL[i]);
+        g.CL[i] = P<int4>(h->CL[i]);
+    }
+    g.acc = P<unsigned long long>(h->acc);
     g.R[0] = P<int32_t>(h->R);
     g.R[1] = P<int32_t>(h->R2);
     g.clcap = h->clcap;
@@ -542,9 +544,9 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
               dev_get(h, h->upstar, 4 * N) && dev_get(h, h->off, 8 * N) && dev_get(h, h->cap, 4 * N) &&
               dev_get(h, h->tomb, 4 * N) && dev_get(h, h->stamp, 4 * N) && dev_get(h, h->dlv, 4 * N) &&
               dev_get(h, h->inc, 4 * N) && dev_get(h, h->pool, 4 * (size_t)h->pool_cap) &&
-              dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->F[0], 4 * N) &&
-              dev_get(h, h->F[1], 4 * N) && dev_get(h, h->M[0], 16 * N) && dev_get(h, h->M[1], 16 * N) &&
-              dev_get(h, h->TL[0], 16 * N) && dev_get(h, h->TL[1], 16 * N) && dev_get(h, h->P[0], 32 * N) &&
+              dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->acc, 8 * N) &&
+              dev_get(h, h->M[0], 16 * N) && dev_get(h, h->M[1], 16 * N) && dev_get(h, h->TL[0], 16 * N) &&
+              dev_get(h, h->TL[1], 16 * N) && dev_get(h, h->TL[2], 16 * N) && dev_get(h, h->P[0], 32 * N) &&
               dev_get(h, h->P[1], 32 * N) && dev_get(h, h->R, 4 * N) && dev_get(h, h->R2, 4 * N) && dev_get(h, h->bins, 4 * (K + 1)) &&
               dev_get(h, h->levlist, 4 * (K + 1)) && alloc_chunk_lists(h);
     if (!ok) {
@@ -568,6 +570,7 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
     cudaMemsetAsync(h->stamp.p, 0, 4 * N, s);
     cudaMemsetAsync(h->dlv.p, 0xff, 4 * N, s);
     cudaMemsetAsync(h->inc.p, 0, 4 * N, s);
+    cudaMemsetAsync(h->acc.p, 0, 8 * N, s);
     cudaMemsetAsync(h->pool_top.p, 0, 8, s);
     cudaStreamSynchronize(s);
     if (cuda_check(h) != PLDS_OK) {

@@ -885,192 +885,264 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
     return T.sync();
 }
 
-// Effects of a mover (l -> l+1) on its neighbour w whose level word is raw:
-// a neighbour on l stays below (counted into the mover's up decrement), one on
-// l+1 gains an up-neighbour and becomes a candidate, one on l+2 gains an
-// up*-neighbour.  Returns true if w must be pushed to the next frontier.
-__device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t snext,
-                                           int &cnt_l) {
-    if (!valid_id(g, w) || (raw & kMoveFlag)) return false;  // empty slot, or w moved up in this round as well
-    if (raw == l) {
+// ---------------------------------------------------------------------------
+// Insertion rounds, one team barrier per level.
+//
+// Round l moves the movers of level l (the vertices on l that violate Invariant
+// 1) to l + 1 and applies their effects: a neighbour left on l is no longer an
+// up-neighbour of the mover; a neighbour on l + 1 gains an up-neighbour; one on
+// l + 2 gains an up*-neighbour.  The movers of level l + 1 are found while round l
+// runs, so no separate candidate phase is needed:
+//   - a vertex on l + 1 that is not an initial candidate satisfies Invariant 1
+//     before round l and its up-degree only grows during it, so it violates on
+//     l + 1 exactly when one arrival takes its up-degree past the cutoff: the
+//     thread whose atomic add sees the old value equal to the cutoff marks it;
+//   - initial candidates on l + 1 are tested during round l (up-degrees only grow,
+//     so a test that passes is final; one that fails is caught by the arrival
+//     that crosses);
+//   - a mover of level l violates again on l + 1 iff its up-degree minus its
+//     neighbours left on l exceeds the cutoff; the scan of its last table chunk
+//     (per-vertex chunk counter) decides, nobody else touching its up-degree.
+// Movers of level l carry the flag of l's parity in their level word from their
+// marking (during round l - 1, where they still read as level l) until the end of
+// round l, whose readers see "mover of l" for a word with that flag and level l or
+// l + 1; the flag of the other parity is ignored.  A level with no movers jumps
+// to the next initial-candidate level, tested in a phase of its own.  Every flag
+// is cleared at the end.  The result is the same as rounds evaluated one level
+// after another (the same-sequence lemma): the marks depend only on final counts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t level_flag(int32_t l) { return (l & 1) ? kFlagOdd : kFlagEven; }
+
+// Effects of a mover of level l on its neighbour w (level word raw).  Returns true
+// if w became a mover of level l + 1 here.
+__device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t fcur,
+                                           int32_t fnext, int32_t cut_next, int &cnt_l) {
+    if (!valid_id(g, w)) return false;  // empty slot or tombstone
+    const int32_t f = raw & kLevelMask;
+    if ((raw & fcur) && (f == l || f == l + 1)) return false;  // a mover of level l as well
+    if (f == l) {
         cnt_l++;
-    } else if (raw == l + 1) {
-        atomicAdd(&g.up[w], 1);
-        return atomicExch(&g.stamp[w], snext) != snext;
-    } else if (raw == l + 2) {
+    } else if (f == l + 1) {
+        if (atomicAdd(&g.up[w], 1) == cut_next) return !(atomicOr(&g.level[w], fnext) & fnext);
+    } else if (f == l + 2) {
         atomicAdd(&g.upstar[w], 1);
     }
     return false;
 }
 
+// A mover of level l whose whole table has been scanned (total = its neighbours
+// left on l): new up* = old up (its neighbours on l or above), new up = old up -
+// total, level l + 1; returns true if it violates Invariant 1 on l + 1 as well.
+__device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, int32_t total, int32_t l,
+                                                 int32_t fcur, int32_t fnext, int32_t cut_next) {
+    const int32_t old_up = g.up[v];
+    const int32_t nu = old_up - total;
+    g.upstar[v] = old_up;
+    g.up[v] = nu;
+    const bool again = nu > cut_next;
+    g.level[v] = (l + 1) | fcur | (again ? fnext : 0);
+    return again;
+}
+
+// Queue the table scans of the lanes' newly marked vertices.
+__device__ __forceinline__ void enqueue_marked(const GraphCtx &g, const RoundStage &st, bool mk, int32_t w,
+                                               int32_t *wsm) {
+    int32_t c = 0;
+    int64_t off = 0;
+    if (mk) {
+        c = g.cap[w];
+        off = g.off[w];
+    }
+    enqueue_mover(g, st, mk, w, 0, c, off, wsm);
+}
+
+// Test the initial candidates S[s_lo, s_hi) on level L against Invariant 1.
 template <class Team>
-__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base, const int32_t *sh_upmax, int32_t *wsm,
-                           RoundStage st) {
+__device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &st, int32_t s_lo, int32_t s_hi,
+                                 int32_t L, int32_t cut, int32_t *wsm) {
+    const int32_t fl = level_flag(L);
+    for (int i0 = s_lo + T.wid() * 32; i0 < s_hi; i0 += T.nwarps() * 32) {
+        const int i = i0 + lane_id();
+        bool mk = false;
+        int32_t v = 0;
+        if (i < s_hi) {
+            v = g.S[i];
+            const int32_t raw = g.level[v];
+            if ((raw & kLevelMask) != L) report(g, kErrInternal, 6, v, raw, L);
+            else if (g.up[v] > cut) mk = !(atomicOr(&g.level[v], fl) & fl);
+        }
+        enqueue_marked(g, st, mk, v, wsm);
+    }
+}
+
+template <class Team>
+__device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0;
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
-    for (int r = 0;; ++r) {
-        const int p = r & 1, q = p ^ 1;
-        // which level does this round process?  (same decision in every thread)
-        const int32_t fc = g.ctl->fcnt[p], sp = g.ctl->spos[p], prev = g.ctl->slevel[p];
-        const int32_t sl = sp < g.ctl->nlev ? g.levlist[sp] : kInf;
-        int32_t l = fc > 0 ? prev + 1 : kInf;
-        if (sl < l) l = sl;
-        if (l == kInf) break;
-        if (l >= g.K - 1 || r > g.K + 2) {  // the top group is never violated
-            if (T.leader()) report(g, kErrInternal, 5, l, r, fc);
+    const int32_t nlev = g.ctl->nlev;
+    int spos = 0;
+    int32_t l = nlev > 0 ? g.levlist[spos++] : 0;
+    bool scan = false;  // this phase scans the movers of l (else it tests the initial candidates on l)
+    for (int k = 0; nlev > 0; ++k) {
+        if ((scan && l >= g.K - 1) || k > 2 * g.K + 4) {  // the top group is never violated
+            if (T.leader()) report(g, kErrInternal, 5, l, k, 0);
             return false;
         }
-        int32_t s_lo = 0, s_hi = 0;
-        if (sl == l) {
-            s_lo = l == 0 ? 0 : g.bins[l - 1];
-            s_hi = g.bins[l];
+        const int cur = k % 3, nxt = (k + 1) % 3, old = (k + 2) % 3;
+        const uint64_t t_phase = (g.trace && T.leader()) ? global_ns() : 0;
+        int32_t tlc = 0, clc = 0, m = 0;
+        if (T.leader()) {  // the lists of phase k - 1 are done with; phase k + 1 fills them next
+            g.ctl->itl[old] = 0;
+            g.ctl->icl[old] = 0;
+            g.ctl->imcnt[old] = 0;
         }
-        if (T.leader()) {
-            g.ctl->slevel[q] = l;
-            g.ctl->spos[q] = sl == l ? sp + 1 : sp;
-            g.ctl->mcnt[q] = 0;
-            g.ctl->tlcnt[q] = 0;
-            g.ctl->clcnt[q] = 0;
-        }
-        const int32_t scur = sid_of(stamp_base, l), snext = sid_of(stamp_base, l + 1);
-        const int32_t cut = sh_upmax[l / g.Lg];
-        st.f.gcnt = &g.ctl->fcnt[q];
-        st.f.glist = g.F[q];
-        st.f.gcap = g.n;
-        st.tl.gcnt = &g.ctl->tlcnt[p];
-        st.tl.glist = g.TL[p];
+        st.tl.gcnt = &g.ctl->itl[nxt];
+        st.tl.glist = g.TL[nxt];
         st.tl.gcap = g.n;
-        st.cl.gcnt = &g.ctl->clcnt[p];
-        st.cl.glist = g.CL[p];
+        st.cl.gcnt = &g.ctl->icl[nxt];
+        st.cl.glist = g.CL[nxt];
         st.cl.gcap = g.clcap;
-        const uint64_t t_round = (g.trace && T.leader()) ? global_ns() : 0;
-        // Phase A: candidates on level l = frontier F[p] plus initial candidates at l.
-        const int32_t nitems = fc + (s_hi - s_lo);
-        for (int i0 = T.wid() * 32; i0 < nitems; i0 += T.nwarps() * 32) {
-            const int i = i0 + lane;
-            bool valid = i < nitems, mover = false;
-            int32_t v = 0, upv = 0, c = 0;
-            int64_t off = 0;
-            if (valid) {
-                if (i < fc) {
-                    v = g.F[p][i];
-                } else {
-                    // skip if v is also in F: F entries carry scur, or snext once their
-                    // copy has already moved v in this phase
-                    v = g.S[s_lo + (i - fc)];
-                    const int32_t old = atomicExch(&g.stamp[v], scur);
-                    valid = old != scur && old != snext;
-                }
+        if (!scan) {
+            const int32_t s_lo = l == 0 ? 0 : g.bins[l - 1], s_hi = g.bins[l];
+            ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm);
+        } else {
+            m = g.ctl->imcnt[cur];
+            tlc = g.ctl->itl[cur];
+            clc = g.ctl->icl[cur];
+            if (T.leader()) {
+                g.ctl->st[kStRounds] += 1;
+                g.ctl->st[kStMoves] += (unsigned long long)m;
             }
-            if (valid) {
-                const int32_t raw = g.level[v];
-                upv = g.up[v];
-                c = g.cap[v];  // fetched with the level: needed if v moves
-                off = g.off[v];
-                if ((raw & kLevelMask) != l) {
-                    report(g, kErrInternal, 6, v, raw, l);
-                } else {
-                    mover = upv > cut;  // Invariant 1 violated on level l
-                    if (mover) {
-                        g.level[v] = (l + 1) | kMoveFlag;
-                        g.upstar[v] = upv;  // Z_l is unchanged by the round: new up* = old up
-                        g.stamp[v] = snext;
-                    } else if (raw & kMoveFlag) {
-                        g.level[v] = l;
+            const int32_t fcur = level_flag(l), fnext = level_flag(l + 1);
+            const int32_t cut_next = sh_upmax[(l + 1) / g.Lg];
+            if (spos < nlev && g.levlist[spos] == l + 1)  // initial candidates on l + 1
+                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm);
+            // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
+            for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
+                const int i = i0 + lane;
+                const int4 it = i < tlc ? g.TL[cur][i] : make_int4(0, 0, 0, 0);
+                const bool have = i < tlc && item_ok(g, it, it.y);
+                const int ng = have ? (1 << it.y) >> 2 : 0;
+                const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
+                int cnt_l = 0;
+                for (int j0 = 0; j0 < maxg; j0 += 4) {
+                    int32_t ws[16], lv[16];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int4 s4 = j0 + j < ng ? pool4[it.z + j0 + j] : empty4();
+                        ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lv[q] = valid_id(g, ws[q]) ? g.level[ws[q]] : 0;
+                    unsigned push = 0;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        visits += ws[q] >= 0;
+                        if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cnt_l)) push |= 1u << q;
+                    }
+                    scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const bool mk = (push >> q) & 1u;
+                        if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
                     }
                 }
+                const bool again = have && ins_finish_mover(g, it.x, cnt_l, l, fcur, fnext, cut_next);
+                enqueue_mover(g, st, again, it.x, 0, have ? 1 << it.y : 0, (int64_t)it.z * 4, wsm);
             }
-            stage_push(st.f, mover, v);
-            enqueue_mover(g, st, mover, v, upv, c, off, wsm);
-        }
-        const uint64_t t_a1 = (g.trace && T.leader()) ? global_ns() : 0;
-        stage_flush_round(g, st, 7u);
-        if (threadIdx.x == 0 && *st.movers) {
-            atomicAdd(&g.ctl->mcnt[p], *st.movers);
-            *st.movers = 0;
-        }
-        if (!T.sync()) return false;
-        // Phase B: scan the movers' neighbours.
-        const uint64_t t_mid = (g.trace && T.leader()) ? global_ns() : 0;
-        if (T.leader()) {
-            const int32_t mc = g.ctl->mcnt[p];
-            if (mc > 0) g.ctl->st[kStRounds] += 1;
-            g.ctl->st[kStMoves] += (unsigned long long)mc;
-            g.ctl->fcnt[p] = 0;
-        }
-        // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
-        const int32_t tlc = g.ctl->tlcnt[p];
-        for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
-            const int i = i0 + lane;
-            const int4 it = i < tlc ? g.TL[p][i] : make_int4(0, 0, 0, 0);
-            const int ng = (i < tlc && item_ok(g, it, it.y)) ? (1 << it.y) >> 2 : 0;
-            const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
-            int cnt_l = 0;
-            for (int j0 = 0; j0 < maxg; j0 += 4) {
+            // chunk items: four per warp iteration, all loads of a step issued together
+            for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
+                int4 it[4];
+                bool ok[4], in[4];
                 int32_t ws[16], lv[16];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int4 s4 = j0 + j < ng ? pool4[it.z + j0 + j] : empty4();
-                    ws[4 * j] = s4.x; ws[4 * j + 1] = s4.y; ws[4 * j + 2] = s4.z; ws[4 * j + 3] = s4.w;
+                for (int u = 0; u < 4; ++u) {
+                    const int cu = c0 + u * T.nwarps();
+                    it[u] = cu < clc ? g.CL[cur][cu] : make_int4(0, 0, 0, 0);
+                    ok[u] = cu < clc && item_ok(g, it[u], it[u].y & 31);
+                    const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
+                    in[u] = ok[u] && j < ((1 << (it[u].y & 31)) >> 2);
+                    const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
+                    ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
+                for (int q = 0; q < 16; ++q) lv[q] = valid_id(g, ws[q]) ? g.level[ws[q]] : 0;
+                int cl4[4] = {0, 0, 0, 0};
                 unsigned push = 0;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    visits += ws[k] >= 0;
-                    if (ins_effect(g, ws[k], lv[k], l, snext, cnt_l)) push |= 1u << k;
+                for (int q = 0; q < 16; ++q) {
+                    visits += ws[q] >= 0;
+                    if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cl4[q >> 2])) push |= 1u << q;
                 }
-                scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
-                stage_push_masked(st.f, push, ws);
-            }
-            if (i < tlc && cnt_l) atomicSub(&g.up[it.x], cnt_l);
-        }
-        // chunk items: four per warp iteration, all loads of a step issued together
-        const int32_t clc = g.ctl->clcnt[p];
-        for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
-            int4 it[4];
-            bool in[4];
-            int32_t ws[16], lv[16];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int cu = c0 + u * T.nwarps();
-                it[u] = cu < clc ? g.CL[p][cu] : make_int4(0, 0, 0, 0);
-                const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
-                in[u] = cu < clc && item_ok(g, it[u], it[u].y & 31) && j < ((1 << (it[u].y & 31)) >> 2);
-                const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
-                ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
-            }
+                for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) lv[k] = valid_id(g, ws[k]) ? g.level[ws[k]] : 0;
-            int cl4[4] = {0, 0, 0, 0};
-            unsigned push = 0;
+                for (int q = 0; q < 16; ++q) {
+                    const bool mk = (push >> q) & 1u;
+                    if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
+                }
+                // the last chunk of a table to finish completes its mover
+                unsigned again = 0;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                visits += ws[k] >= 0;
-                if (ins_effect(g, ws[k], lv[k], l, snext, cl4[k >> 2])) push |= 1u << k;
-            }
+                for (int u = 0; u < 4; ++u) {
+                    const int cnt = warp_sum(cl4[u]);
+                    if (lane == 0 && ok[u]) {
+                        const int lg = it[u].y & 31;
+                        const int nch = max(1, (1 << lg) / kChunk);
+                        bool last = true;
+                        int32_t total = cnt;
+                        if (nch > 1) {
+                            const unsigned long long o =
+                                atomicAdd(&g.acc[it[u].x], (1ull << 32) | (unsigned long long)(uint32_t)cnt);
+                            last = (int)(o >> 32) + 1 == nch;
+                            total = (int32_t)(uint32_t)(o & 0xffffffffull) + cnt;
+                            if (last) g.acc[it[u].x] = 0ull;
+                        }
+                        if (last && ins_finish_mover(g, it[u].x, total, l, fcur, fnext, cut_next)) again |= 1u << u;
+                    }
+                }
+                again = __shfl_sync(kFull, again, 0);
+                int4 mine = it[0];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
-            stage_push_masked(st.f, push, ws);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int cu = warp_sum(cl4[u]);
-                if (lane == 0 && cu) atomicSub(&g.up[it[u].x], cu);
+                for (int u = 1; u < 4; ++u)
+                    if (lane == u) mine = it[u];
+                const bool cont = lane < 4 && ((again >> lane) & 1u);
+                enqueue_mover(g, st, cont, mine.x, 0, cont ? 1 << (mine.y & 31) : 0, (int64_t)mine.z * 4, wsm);
             }
         }
-        const uint64_t t_b1 = (g.trace && T.leader()) ? global_ns() : 0;
-        stage_flush_round(g, st, 1u);
+        const uint64_t t_work = (g.trace && T.leader()) ? global_ns() : 0;
+        stage_flush_round(g, st, 6u);
+        if (threadIdx.x == 0 && *st.movers) {
+            atomicAdd(&g.ctl->imcnt[nxt], *st.movers);
+            *st.movers = 0;
+        }
         if (!T.sync()) return false;
         if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
             int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
             const uint64_t t_end = global_ns();
-            rec[0] = l; rec[1] = nitems; rec[2] = g.ctl->mcnt[p]; rec[3] = tlc; rec[4] = clc;
-            rec[5] = (int32_t)(t_a1 - t_round); rec[6] = (int32_t)(t_mid - t_a1);
-            rec[7] = (int32_t)(t_b1 - t_mid); rec[8] = (int32_t)(t_end - t_b1);
-            rec[9] = rec[10] = rec[11] = 0;
+            rec[0] = l; rec[1] = scan ? 1 : 0; rec[2] = m; rec[3] = tlc; rec[4] = clc;
+            rec[5] = (int32_t)(t_work - t_phase); rec[6] = (int32_t)(t_end - t_work);
+            rec[7] = rec[8] = rec[9] = rec[10] = rec[11] = 0;
         }
+        // the next phase: the movers of l + 1 (after a scan) or of l (after a test),
+        // else the initial candidates of the next level that has some
+        if (scan) {
+            if (spos < nlev && g.levlist[spos] == l + 1) ++spos;
+            ++l;
+        }
+        if (g.ctl->imcnt[nxt] > 0) {
+            scan = true;
+            continue;
+        }
+        if (spos >= nlev) break;
+        l = g.levlist[spos++];
+        scan = false;
+    }
+    // clear the movers' flags (every vertex: flags sit only on vertices that moved)
+    for (int64_t v = T.tid(); v < g.n; v += T.nthreads()) {
+        const int32_t raw = g.level[v];
+        if (raw & ~kLevelMask) g.level[v] = raw & kLevelMask;
     }
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
@@ -1078,7 +1150,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
     }
-    return true;
+    return T.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1605,7 +1677,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
             tmark[nmark++] = global_ns();
             trace_steps(g, tmark, nmark, -1);
         }
-        ins_rounds(T, g, in.stamp_base, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
+        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
     } else {
         if (T.leader()) {
             g.ctl->nextmin[0] = kInf;

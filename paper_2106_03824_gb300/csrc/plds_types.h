@@ -7,8 +7,11 @@ namespace pl {
 
 constexpr int32_t kEmpty = -1;          // hash slot never used since the last rebuild
 constexpr int32_t kTomb = -2;           // hash slot of a deleted neighbour
-constexpr int32_t kMoveFlag = 1 << 30;  // level bit: vertex moved up in the current round
-constexpr int32_t kLevelMask = kMoveFlag - 1;
+// Insertion rounds mark the movers of level l in the level word with the flag of
+// l's parity; the level itself is the word & kLevelMask.  Flags never survive a batch.
+constexpr int32_t kFlagEven = 1 << 30;
+constexpr int32_t kFlagOdd = 1 << 29;
+constexpr int32_t kLevelMask = kFlagOdd - 1;
 constexpr int32_t kInf = 0x7fffffff;
 constexpr int kMaxGroups = 512;        // groups (t+1) supported by the device tables
 constexpr int kWindow = 256;           // desire-level histogram window (levels)
@@ -41,8 +44,10 @@ struct Ctl {
     int32_t tcount;              // touched vertices
     int32_t shrink_used;         // arena ints used by table shrinking
     unsigned long long grow_total;  // slots requested by growing tables
-    int32_t fcnt[2];      // insertion frontier sizes (by round parity)
-    int32_t mcnt[2];      // movers (by round parity)
+    int32_t imcnt[3];     // insertion: movers marked for a phase (phase index mod 3)
+    int32_t itl[3];       // insertion: thread-mode scan items of a phase
+    int32_t icl[3];       // insertion: chunk scan items of a phase
+    int32_t mcnt[2];      // table growth / deletion movers
     int32_t tlcnt[2];     // thread-mode movers
     int32_t clcnt[2];     // chunk items
     int32_t slevel[2];    // insertion round state: current level
@@ -92,10 +97,10 @@ struct GraphCtx {
     int32_t *S;            // candidates sorted by level [tcap]
     int32_t *bins;         // [K+1] level histogram / offsets
     int32_t *levlist;      // [K] distinct candidate levels
-    int32_t *F[2];         // insertion frontier [n]
+    unsigned long long *acc;  // [n] insertion: per mover {chunks done << 32 | neighbours left below}
     int4 *M[2];            // movers {v, aux, cap, -} [n]
-    int4 *TL[2];           // thread-mode scan items {v, log2 cap, offset/4, aux} [n]
-    int4 *CL[2];           // chunk scan items {v, chunk<<5 | log2 cap, offset/4, aux} [clcap]
+    int4 *TL[3];           // thread-mode scan items {v, log2 cap, offset/4, aux} [n]
+    int4 *CL[3];           // chunk scan items {v, chunk<<5 | log2 cap, offset/4, aux} [clcap]
     int64_t clcap;
     int4 *P[2];            // pending {v, dl, -, -} [2n]
     int32_t *R[2];         // desire-level recompute candidates; R[1]: violators to evaluate [n]
