@@ -956,6 +956,45 @@ __device__ __forceinline__ void enqueue_marked(const GraphCtx &g, const RoundSta
     enqueue_mover(g, st, mk, w, 0, c, off, wsm);
 }
 
+// Marked neighbours wait in a per-warp buffer (kMarkCap ids in the warp's shared
+// scratch, after the 160 ints enqueue_mover uses) and are queued 32 at a time, so
+// their table lookups are issued together.
+constexpr int kMarkCap = 256;
+
+__device__ __forceinline__ void marks_flush(const GraphCtx &g, const RoundStage &st, int32_t *mbuf, int &mc,
+                                            int32_t *wsm) {
+    for (int b = 0; b < mc; b += 32) {
+        const int i = b + lane_id();
+        const bool mk = i < mc;
+        enqueue_marked(g, st, mk, mk ? mbuf[i] : 0, wsm);
+    }
+    __syncwarp();
+    mc = 0;
+}
+
+// Append the lanes' marked neighbours (bits of push over ws); mc is warp-uniform.
+__device__ __forceinline__ void marks_add(const GraphCtx &g, const RoundStage &st, unsigned push,
+                                          const int32_t (&ws)[16], int32_t *mbuf, int &mc, int32_t *wsm) {
+    int tot;
+    const int ex = warp_exclusive(__popc(push), &tot);
+    if (tot == 0) return;
+    if (mc + tot > kMarkCap) marks_flush(g, st, mbuf, mc, wsm);
+    if (tot > kMarkCap) {  // more than the buffer holds: queue them one slot position at a time
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const bool mk = (push >> q) & 1u;
+            if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
+        }
+        return;
+    }
+    int pos = mc + ex;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if ((push >> q) & 1u) mbuf[pos++] = ws[q];
+    __syncwarp();
+    mc += tot;
+}
+
 // Test the initial candidates S[s_lo, s_hi) on level L against Invariant 1.
 template <class Team>
 __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &st, int32_t s_lo, int32_t s_hi,
@@ -981,6 +1020,8 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     const int32_t nlev = g.ctl->nlev;
+    int32_t *mbuf = wsm + 160;
+    int mc = 0;
     int spos = 0;
     int32_t l = nlev > 0 ? g.levlist[spos++] : 0;
     bool scan = false;  // this phase scans the movers of l (else it tests the initial candidates on l)
@@ -1042,11 +1083,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                         if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cnt_l)) push |= 1u << q;
                     }
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const bool mk = (push >> q) & 1u;
-                        if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
-                    }
+                    marks_add(g, st, push, ws, mbuf, mc, wsm);
                 }
                 const bool again = have && ins_finish_mover(g, it.x, cnt_l, l, fcur, fnext, cut_next);
                 enqueue_mover(g, st, again, it.x, 0, have ? 1 << it.y : 0, (int64_t)it.z * 4, wsm);
@@ -1077,11 +1114,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const bool mk = (push >> q) & 1u;
-                    if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
-                }
+                marks_add(g, st, push, ws, mbuf, mc, wsm);
                 // the last chunk of a table to finish completes its mover
                 unsigned again = 0;
 #pragma unroll
@@ -1110,6 +1143,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 const bool cont = lane < 4 && ((again >> lane) & 1u);
                 enqueue_mover(g, st, cont, mine.x, 0, cont ? 1 << (mine.y & 31) : 0, (int64_t)mine.z * 4, wsm);
             }
+            marks_flush(g, st, mbuf, mc, wsm);
         }
         const uint64_t t_work = (g.trace && T.leader()) ? global_ns() : 0;
         stage_flush_round(g, st, 6u);
