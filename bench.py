@@ -125,7 +125,8 @@ def make_stream(scale: int, batch: int, seed: int = 1):
     return e, ins, dele, steps
 
 
-def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3):
+def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3, levels_per_group=0,
+                  sizes=(1_000_000, 100_000)):
     """The experiments' Ins / Del / Mix protocols on the same graph, plain form,
     device-resident inputs: Ins all edges from empty and Del them all, in batches of
     1e6 and 1e5; Mix = 50/50 insert/delete batches of 1e6 on a 90 %-loaded graph
@@ -149,14 +150,14 @@ def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3):
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
     out = {}
-    for B in (1_000_000, 100_000):
+    for B in sizes:
         tag = "1e6" if B == 1_000_000 else "1e5"
-        g = P.PLDS(n)
+        g = P.PLDS(n, levels_per_group=levels_per_group)
         out[f"ins_{tag}"] = timed(g, [(g.insert, ins_d[s:s + B]) for s in range(0, ins_d.shape[0], B)])
         out[f"del_{tag}"] = timed(g, [(g.delete, del_d[s:s + B]) for s in range(0, del_d.shape[0], B)])
         g.close()
     pre, mixes = W.mix_stream(e, 1_000_000, mix_batches, load=0.9, seed=seed)
-    g = P.PLDS(n)
+    g = P.PLDS(n, levels_per_group=levels_per_group)
     pre_d = torch.from_numpy(pre).cuda()
     for s in range(0, pre_d.shape[0], 1_000_000):
         g.insert(pre_d[s:s + 1_000_000])
@@ -622,6 +623,11 @@ def main():
     protocols = None
     if world == 1 and not args.no_protocols:
         protocols = run_protocols(P, n, e, ins_d, del_d)
+        # the paper's optimised variant: ceil(log_{1+delta} m / 50) levels per group
+        lg_opt = P.opt_levels_per_group(int(e.shape[0]))
+        protocols["plds_opt"] = {"levels_per_group": lg_opt,
+                                 **run_protocols(P, n, e, ins_d, del_d, levels_per_group=lg_opt,
+                                                 sizes=(1_000_000,))}
 
     phases = {}
     for kind in ("ins", "del"):

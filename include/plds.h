@@ -178,6 +178,16 @@ int plds_params(plds_t *h, int32_t *out);
  * Each array has `groups` entries (out[2] of plds_params).  Host pointers. */
 int plds_tables(plds_t *h, int32_t *upmax, int32_t *dnmin);
 
+/* Levels per group of the paper's optimised variant PLDSOpt (experiments
+ * section, "Evaluated Algorithms"): ceil(log_{1+delta}(m) / 50), at least 1, for a
+ * graph of about m edges -- pass it as levels_per_group to plds_create_ex.  Exact:
+ * the smallest L >= 1 with (1+delta)^(50 L) >= m, delta read as a rational with
+ * denominator 10^6.  m must be in [0, 2^32); returns PLDS_EINVAL otherwise or for
+ * a delta so small that the test needs more than 20000 bits.  With fewer levels
+ * per group the batch rules and both invariants are unchanged, but the
+ * (2+3/lambda)(1+delta) approximation bound is no longer guaranteed. */
+int32_t plds_opt_levels_per_group(int64_t m, double delta);
+
 /* Use another stream for subsequent calls. */
 int plds_set_stream(plds_t *h, void *stream);
 

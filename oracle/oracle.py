@@ -62,6 +62,8 @@ def lib():
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, P, P,
                                        ctypes.c_int32]
         L.orc_exact_coreness.argtypes = [ctypes.c_int32, P, ctypes.c_int64, P]
+        L.orc_opt_levels_per_group.argtypes = [ctypes.c_int64, ctypes.c_double]
+        L.orc_opt_levels_per_group.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -73,6 +75,14 @@ def _ptr(a: np.ndarray):
 def _edges(e) -> np.ndarray:
     a = np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, 2))
     return a
+
+
+def opt_levels_per_group(m: int, delta: float = 0.4) -> int:
+    """PLDSOpt's ceil(log_{1+delta}(m) / 50) levels per group (at least 1), exact."""
+    r = lib().orc_opt_levels_per_group(int(m), float(delta))
+    if r < 0:
+        raise ValueError(f"orc_opt_levels_per_group({m}, {delta}) = {r}")
+    return r
 
 
 def tables(n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0):

@@ -137,6 +137,30 @@ static int to_rational(double x, int64_t *num, int64_t *den) {
     return 0;
 }
 
+/*
+ * PLDSOpt's levels per group (experiments section, "Evaluated Algorithms", and the
+ * implementation paragraph that divides the group size by 50): ceil(log_{1+delta}
+ * m / 50), at least 1.  Decided exactly as the smallest L >= 1 with
+ * (1+delta)^(50 L) >= m, i.e. (dnum+dden)^(50 L) >= m * dden^(50 L).
+ * m must be below 2^32 and dnum+dden below 2^32; ORC_EINVAL otherwise, and when the
+ * powers outgrow the bignum (very small delta).
+ */
+int32_t orc_opt_levels_per_group(int64_t m, double delta) {
+    int64_t p, q;
+    if (m < 0 || m > 0xffffffffLL || to_rational(delta, &p, &q) || p + q > 0xffffffffLL) return ORC_EINVAL;
+    static bignum num, den, rhs;
+    bn_from(&num, 1);
+    bn_from(&den, 1);
+    for (int32_t L = 1; L <= 1 << 20; ++L) {
+        for (int k = 0; k < 50; ++k)
+            if (bn_mul_small(&num, (uint64_t)(p + q)) || bn_mul_small(&den, (uint64_t)q)) return ORC_EINVAL;
+        rhs = den;
+        if (bn_mul_small(&rhs, (uint64_t)m)) return ORC_EINVAL;
+        if (bn_cmp(&num, &rhs) >= 0) return L;
+    }
+    return ORC_EINVAL;
+}
+
 #define ORC_MAX_GROUPS 4096
 #define ORC_MAX_LEVELS (1 << 24)
 

@@ -1902,6 +1902,11 @@ extern "C" int plds_server_configure(plds_server_t *sv, int64_t merge_max_edges,
     return set_status(PLDS_OK);
 }
 
+extern "C" int32_t plds_opt_levels_per_group(int64_t m, double delta) {
+    const int32_t r = opt_levels_per_group(m, delta);
+    return r > 0 ? r : PLDS_EINVAL;
+}
+
 extern "C" int plds_server_admission(int64_t pool_cap, int64_t pool_used, int64_t inflight, int64_t need,
                                      int64_t free_bytes) {
     if (pool_cap < 0 || pool_used < 0 || inflight < 0 || need < 0 || free_bytes < 0) return PLDS_EINVAL;

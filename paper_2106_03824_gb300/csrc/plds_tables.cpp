@@ -148,4 +148,24 @@ int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_grou
     return 0;
 }
 
+int32_t opt_levels_per_group(int64_t m, double delta) {
+    if (m < 0 || m > (int64_t)0xffffffffLL || !(delta > 0) || delta > 1e6) return -1;
+    int64_t p = std::llround(delta * 1e6), q = 1000000;
+    if (p <= 0) return -1;
+    const int64_t g = std::gcd(p, q);
+    p /= g;
+    q /= g;
+    if (p + q > (int64_t)0xffffffffLL) return -1;
+    Nat num = Nat::of(1), den = Nat::of(1);
+    for (int32_t L = 1; L <= (1 << 20); ++L) {
+        for (int k = 0; k < 50; ++k) {
+            num = mul(num, (uint32_t)(p + q));
+            den = mul(den, (uint32_t)q);
+        }
+        if (num.bits() > 20000) return -1;
+        if (cmp(num, mul(den, (uint32_t)m)) >= 0) return L;
+    }
+    return -1;
+}
+
 }  // namespace pl

@@ -19,4 +19,9 @@ struct Tables {
 // more than 512 groups or 2^24 levels).
 int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_group, Tables *out);
 
+// Levels per group of the optimised variant: ceil(log_{1+delta}(m) / 50), at least 1
+// (the smallest L >= 1 with (1+delta)^(50 L) >= m, exact).  -1 on invalid input
+// (m outside [0, 2^32), delta not positive, or powers beyond 20000 bits).
+int32_t opt_levels_per_group(int64_t m, double delta);
+
 }  // namespace pl

@@ -121,6 +121,8 @@ def load():
     L.plds_server_destroy.restype = None
     L.plds_server_configure.argtypes = [vp, i64, i64]
     L.plds_server_admission.argtypes = [i64, i64, i64, i64, i64]
+    L.plds_opt_levels_per_group.argtypes = [i64, dbl]
+    L.plds_opt_levels_per_group.restype = i32
     L.plds_last_status.argtypes = []
     L.plds_destroy.argtypes = [vp]
     L.plds_destroy.restype = None
@@ -453,6 +455,15 @@ def tune_search(cost, start: dict | None = None, max_trials: int = 24):
     if k < 0:
         raise PldsError(k, "plds_tune_search")
     return best.knobs(), k
+
+
+def opt_levels_per_group(m: int, delta: float = 0.4) -> int:
+    """Levels per group of PLDSOpt for a graph of about m edges (pass it as
+    levels_per_group); raises on invalid input."""
+    r = load().plds_opt_levels_per_group(int(m), float(delta))
+    if r < 0:
+        raise PldsError(r, "plds_opt_levels_per_group")
+    return r
 
 
 def server_admission(pool_cap: int, pool_used: int, inflight: int, need: int, free_bytes: int) -> int:

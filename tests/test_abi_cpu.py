@@ -93,3 +93,14 @@ def test_tune_search_budget_and_failure(lib):
     # a 1 % gain is below the 2 % threshold: the incumbent stays
     best, _ = P.tune_search(lambda k: 0.99 if k["thread_max_cap"] == 4 else 1.0)
     assert best["thread_max_cap"] == 16
+
+
+def test_opt_levels_per_group_matches_oracle(lib):
+    """The library's exact PLDSOpt group size agrees with the oracle's own bignum."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        d = float(rng.choice([0.05, 0.1, 0.2, 0.4, 0.4211, 0.4212, 1.0, 3.2]))
+        m = int(rng.integers(0, 2**32))
+        assert P.opt_levels_per_group(m, d) == O.opt_levels_per_group(m, d), (m, d)
+    assert lib.plds_opt_levels_per_group(2**32, 0.4) == P.PLDS_EINVAL

@@ -188,6 +188,32 @@ def test_rmat_every_batch(P, scale, batch):
     g.close()
 
 
+def test_pldsopt_every_batch(P):
+    """PLDSOpt (ceil(log_{1+delta} m / 50) levels per group, here 1): the same batch
+    rules on fewer levels; levels, counters and work counts equal the oracle's with
+    the same group size after every batch, and the oracle's invariant checks pass."""
+    scale, batch = 16, 100_000
+    n = 1 << scale
+    e = W.rmat(scale, 16, seed=scale)
+    lg = P.opt_levels_per_group(e.shape[0])
+    assert lg == O.opt_levels_per_group(e.shape[0]) == 1
+    g, o = P.PLDS(n, levels_per_group=lg), O.OraclePLDS(n, levels_per_group=lg)
+    assert g.Lg == lg and g.K == g.G * lg
+    for i, b in enumerate(W.batches(W.shuffled(e, 1), batch)):
+        g.insert(b)
+        o.insert(b)
+        assert o.check() == 0
+        assert_same(g, o, f"opt ins {i}")
+        assert_stats(g, o, f"opt ins {i}")
+    for i, b in enumerate(W.batches(W.shuffled(e, 2), batch)):
+        g.delete(b)
+        o.delete(b)
+        assert o.check() == 0
+        assert_same(g, o, f"opt del {i}")
+        assert_stats(g, o, f"opt del {i}")
+    g.close()
+
+
 def test_tuning_never_changes_results(P):
     n = 1 << 13
     e = W.rmat(13, 16, seed=5)

@@ -355,3 +355,52 @@ def test_out_of_range_rejected_before_any_change():
     assert h.insert([(-1, 3)]) == O.ORC_EINVAL
     assert h.delete([(0, 1), (n + 5, 1)]) == O.ORC_EINVAL
     assert list(h.levels()) == list(lv) and h.edges().shape[0] == m
+
+
+# ----------------------------------------------------------------------------
+# PLDSOpt levels per group (experiments section, "Evaluated Algorithms")
+# ----------------------------------------------------------------------------
+
+def test_opt_levels_per_group_livejournal_example():
+    """The paper's livejournal example (m = 42,851,237): log_1.4(m) = 52.2, so the
+    formula gives ceil(1.04) = 2 at delta = 0.4; it gives 1 only from delta ~ 0.4212
+    up (the text's "1 for all delta < 0.42" has the inequality reversed), and 1 across
+    the [0.8, 6.4] range where the paper reports flat PLDSOpt curves."""
+    m = 42_851_237
+    assert O.opt_levels_per_group(m, 0.4) == 2
+    assert O.opt_levels_per_group(m, 0.4211) == 2
+    assert O.opt_levels_per_group(m, 0.4212) == 1
+    for d in (0.43, 0.8, 1.6, 3.2, 6.4):
+        assert O.opt_levels_per_group(m, d) == 1
+
+
+def test_opt_levels_per_group_closed_forms():
+    # 1.1^50 = 117.39..., 1.1^100 = 13780.61...
+    assert O.opt_levels_per_group(117, 0.1) == 1
+    assert O.opt_levels_per_group(118, 0.1) == 2
+    assert O.opt_levels_per_group(13_780, 0.1) == 2
+    assert O.opt_levels_per_group(13_781, 0.1) == 3
+    # 2^50 > 2^32: one level per group for every m at delta = 1
+    assert O.opt_levels_per_group(2**32 - 1, 1.0) == 1
+    # log <= 0: at least one level
+    assert O.opt_levels_per_group(0, 0.4) == 1
+    assert O.opt_levels_per_group(1, 0.4) == 1
+    with pytest.raises(ValueError):
+        O.opt_levels_per_group(2**32, 0.4)
+    with pytest.raises(ValueError):
+        O.opt_levels_per_group(-1, 0.4)
+
+
+def test_opt_levels_per_group_against_logarithms():
+    """Away from the boundaries, ceil(ln m / ln(1+delta) / 50) in floating point."""
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(400):
+        d = float(rng.choice([0.05, 0.1, 0.2, 0.4, 0.8, 1.6]))
+        m = int(np.exp(rng.uniform(0, np.log(2**32 - 1))))
+        x = math.log(max(m, 1)) / math.log(1 + d) / 50
+        if abs(x - round(x)) < 1e-6:
+            continue
+        assert O.opt_levels_per_group(m, d) == max(1, math.ceil(x)), (m, d)
+        checked += 1
+    assert checked > 350
