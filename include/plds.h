@@ -87,6 +87,9 @@ typedef struct plds_tuning {
     int32_t barrier_sleep_ns; /* pause between polls of a grid-barrier wait (0 = default 32, -1 = none) */
     int32_t block_cap;        /* tables above this many slots get a whole block for desire-levels
                                  and rebuilds, smaller ones a warp (0 = default 4096, else >= 4) */
+    int32_t track_orientation; /* 1 = every plds_batch_insert / plds_batch_delete call saves the
+                                  levels at its start (4n bytes of device memory and one copy)
+                                  so that plds_flips / plds_oriented_updates can report it */
 } plds_tuning;
 
 /*
@@ -187,6 +190,30 @@ int plds_tables(plds_t *h, int32_t *upmax, int32_t *dnmin);
  * per group the batch rules and both invariants are unchanged, but the
  * (2+3/lambda)(1+delta) approximation bound is no longer guaranteed. */
 int32_t plds_opt_levels_per_group(int64_t m, double delta);
+
+/*
+ * Low out-degree orientation (Section "O(alpha) Out-Degree Orientation",
+ * Algorithm 5).  An edge goes from the endpoint on the lower level to the one on
+ * the higher level; on equal levels from the lower id to the higher id (the
+ * reading of Algorithm 5's flip conditions; the section's prose states the
+ * opposite tie rule).  Every vertex's out-degree is at most its up-degree, hence at
+ * most the Invariant-1 cutoff of its level's group.  Edge arrays are int32[B][2],
+ * outputs int32 arrays; host or device pointers.
+ *   plds_orient: tail[i] = the endpoint edge i goes from, -1 if the edge is not in
+ *     the graph or an id is out of range.
+ *   plds_out_degrees: out[v] = number of edges going from v (int32[n]).
+ *   plds_flips: F of the last batch call (which must have been a plds_batch_insert /
+ *     plds_batch_delete made with tuning.track_orientation = 1, and the last call
+ *     changing the graph): every edge present before and after it whose orientation
+ *     changed, as (tail, head) BEFORE the flip.  Up to cap pairs go to out, in no
+ *     particular order; *count gets the total.  PLDS_EINVAL if tracking was off.
+ *   plds_oriented_updates: J of that call: its valid updates as (tail, head),
+ *     insertions oriented after the call, deletions before it.
+ */
+int plds_orient(plds_t *h, const int32_t *edges, int64_t B, int32_t *tail);
+int plds_out_degrees(plds_t *h, int32_t *out);
+int plds_flips(plds_t *h, int32_t *out, int64_t cap, int64_t *count);
+int plds_oriented_updates(plds_t *h, int32_t *out, int64_t cap, int64_t *count);
 
 /* Use another stream for subsequent calls. */
 int plds_set_stream(plds_t *h, void *stream);

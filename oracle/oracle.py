@@ -62,6 +62,11 @@ def lib():
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, P, P,
                                        ctypes.c_int32]
         L.orc_exact_coreness.argtypes = [ctypes.c_int32, P, ctypes.c_int64, P]
+        L.orc_track.argtypes = [P, ctypes.c_int]
+        L.orc_orient.argtypes = [P, P, ctypes.c_int64, P]
+        L.orc_out_degrees.argtypes = [P, P]
+        for name in ("orc_flips", "orc_oriented_updates"):
+            getattr(L, name).argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.orc_opt_levels_per_group.argtypes = [ctypes.c_int64, ctypes.c_double]
         L.orc_opt_levels_per_group.restype = ctypes.c_int32
         _lib = L
@@ -188,3 +193,35 @@ class OraclePLDS:
         out = np.zeros((m.value, 2), np.int32)
         lib().orc_edges(self._h, _ptr(out))
         return out
+
+    # orientation (Algorithm 5)
+    def track(self, on: bool = True):
+        lib().orc_track(self._h, 1 if on else 0)
+
+    def orient(self, edges) -> np.ndarray:
+        e = _edges(edges)
+        out = np.zeros(e.shape[0], np.int32)
+        lib().orc_orient(self._h, _ptr(e), e.shape[0], _ptr(out))
+        return out
+
+    def out_degrees(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        lib().orc_out_degrees(self._h, _ptr(out))
+        return out
+
+    def _pairs(self, fn) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        rc = fn(self._h, None, 0, ctypes.byref(cnt))
+        if rc != ORC_OK:
+            raise ValueError(f"rc={rc} (tracking off?)")
+        out = np.zeros((max(cnt.value, 1), 2), np.int32)
+        fn(self._h, _ptr(out), cnt.value, ctypes.byref(cnt))
+        return out[:cnt.value]
+
+    def flips(self) -> np.ndarray:
+        """Edges of the last batch whose orientation flipped, (tail, head) before, sorted."""
+        return self._pairs(lib().orc_flips)
+
+    def oriented_updates(self) -> np.ndarray:
+        """The last batch's valid updates oriented as Algorithm 5 returns them, sorted."""
+        return self._pairs(lib().orc_oriented_updates)

@@ -335,6 +335,13 @@ typedef struct {
     int64_t st_rounds, st_moves, st_visits, st_dl_evals, st_dl_visits;
     int32_t st_max_level_moves; /* insert: max levels one vertex climbed; delete: max moves of one vertex */
     int32_t st_dir_error;       /* 1 if a vertex moved against the batch's direction */
+    /* orientation tracking (Algorithm 5): the last batch's levels before it, its
+       kind and its valid (applied) edges */
+    int track;
+    int32_t *old_level;
+    int last_op;                /* 0 insertion, 1 deletion, -1 none */
+    uint64_t *last_keys;
+    int64_t last_m;
 } orc_plds;
 
 static uint64_t ekey(int32_t u, int32_t v) { return ((uint64_t)(uint32_t)u << 32) | (uint32_t)v; }
@@ -470,6 +477,7 @@ orc_plds *orc_create(int32_t n, double delta, double lambda, int32_t lg_override
         return NULL;
     }
     for (int32_t i = 0; i < n; ++i) h->dl[i] = -1;
+    h->last_op = -1;
     return h;
 }
 
@@ -487,6 +495,8 @@ void orc_destroy(orc_plds *h) {
     free(h->dl);
     free(h->map.key);
     free(h->map.val);
+    free(h->old_level);
+    free(h->last_keys);
     free(h->T.upmax);
     free(h->T.dnmin);
     free(h);
@@ -566,11 +576,14 @@ static void reset_stats(orc_plds *h) {
  * mover stays marked only while it still violates Invariant 1 at l+1.
  * bucket[l] lists vertices that may be candidates at level l.
  */
+static int track_batch(orc_plds *h, int op, const uint64_t *keys, int64_t m);
+
 int orc_insert(orc_plds *h, const int32_t *edges, int64_t B) {
     reset_stats(h);
     uint64_t *keys = NULL;
     int64_t m = preprocess(h, edges, B, 0, &keys);
     if (m < 0) return (int)m;
+    if (track_batch(h, 0, keys, m)) { free(keys); return ORC_ENOMEM; }
     const int32_t K = h->T.K;
     int rc = ORC_OK;
     int32_t *start_level = NULL;
@@ -667,6 +680,7 @@ int orc_delete(orc_plds *h, const int32_t *edges, int64_t B) {
     uint64_t *keys = NULL;
     int64_t m = preprocess(h, edges, B, 1, &keys);
     if (m < 0) return (int)m;
+    if (track_batch(h, 1, keys, m)) { free(keys); return ORC_ENOMEM; }
     const int32_t K = h->T.K;
     int rc = ORC_OK;
     ivec *bucket = (ivec *)calloc((size_t)K + 1, sizeof(ivec));
@@ -925,4 +939,130 @@ out:
     free(vert);
     free(bin);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Low out-degree orientation (Section "O(alpha) Out-Degree Orientation",    */
+/* Algorithm 5).                                                             */
+/* An edge goes from the endpoint on the lower level to the one on the       */
+/* higher level; on equal levels from the lower id to the higher id (the     */
+/* reading of Algorithm 5's flip conditions; the section's prose says the    */
+/* opposite, see the design notes).                                          */
+/* ------------------------------------------------------------------------- */
+
+/* 1 if the edge {u, v} goes from u to v under the level array lv */
+static int goes_from(const int32_t *lv, int32_t u, int32_t v) {
+    return lv[u] < lv[v] || (lv[u] == lv[v] && u < v);
+}
+
+/* Keep (1) or stop keeping (0) what orc_flips and orc_oriented_updates need. */
+int orc_track(orc_plds *h, int on) {
+    h->track = on ? 1 : 0;
+    return ORC_OK;
+}
+
+static int track_batch(orc_plds *h, int op, const uint64_t *keys, int64_t m) {
+    if (!h->track) return 0;
+    if (!h->old_level && !(h->old_level = (int32_t *)malloc(sizeof(int32_t) * h->n))) return -1;
+    memcpy(h->old_level, h->level, sizeof(int32_t) * h->n);
+    free(h->last_keys);
+    h->last_keys = (uint64_t *)malloc(sizeof(uint64_t) * (m > 0 ? m : 1));
+    if (!h->last_keys) return -1;
+    if (m > 0) memcpy(h->last_keys, keys, sizeof(uint64_t) * m);
+    h->last_m = m;
+    h->last_op = op;
+    return 0;
+}
+
+/* tail[i] = the endpoint edge i is oriented from, -1 if the edge is absent or an id
+   is out of range */
+int orc_orient(const orc_plds *h, const int32_t *edges, int64_t B, int32_t *tail) {
+    for (int64_t i = 0; i < B; ++i) {
+        int32_t u = edges[2 * i], v = edges[2 * i + 1];
+        if (u < 0 || v < 0 || u >= h->n || v >= h->n || u == v || !has_edge(h, u, v)) {
+            tail[i] = -1;
+            continue;
+        }
+        tail[i] = goes_from(h->level, u, v) ? u : v;
+    }
+    return ORC_OK;
+}
+
+/* out[v] = number of edges oriented away from v */
+int orc_out_degrees(const orc_plds *h, int32_t *out) {
+    for (int32_t v = 0; v < h->n; ++v) {
+        int32_t c = 0;
+        for (int32_t j = 0; j < h->deg[v]; ++j) c += goes_from(h->level, v, h->nbr[v][j]);
+        out[v] = c;
+    }
+    return ORC_OK;
+}
+
+static int in_sorted(const uint64_t *a, int64_t n, uint64_t k) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] == k) return 1;
+        if (a[mid] < k) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0;
+}
+
+/*
+ * F of the last batch: the edges present before and after it whose orientation
+ * changed, each as (tail, head) BEFORE the flip, sorted.  Up to cap pairs are
+ * written to out; *count gets their total.  Needs orc_track(h, 1) before the batch.
+ */
+int orc_flips(const orc_plds *h, int32_t *out, int64_t cap, int64_t *count) {
+    if (!h->track || h->last_op < 0) return ORC_EINVAL;
+    int64_t k = 0;
+    uint64_t *acc = NULL;
+    int64_t acap = 0;
+    for (int32_t u = 0; u < h->n; ++u) {
+        for (int32_t j = 0; j < h->deg[u]; ++j) {
+            int32_t v = h->nbr[u][j];
+            if (v < u) continue; /* each edge once, from its lower endpoint */
+            if (h->last_op == 0 && in_sorted(h->last_keys, h->last_m, ekey(u, v))) continue; /* inserted now */
+            int before = goes_from(h->old_level, u, v), after = goes_from(h->level, u, v);
+            if (before == after) continue;
+            if (k == acap) {
+                acap = acap ? 2 * acap : 64;
+                uint64_t *t = (uint64_t *)realloc(acc, sizeof(uint64_t) * acap);
+                if (!t) { free(acc); return ORC_ENOMEM; }
+                acc = t;
+            }
+            acc[k++] = before ? ekey(u, v) : ekey(v, u);
+        }
+    }
+    if (k > 1) qsort(acc, (size_t)k, sizeof(uint64_t), cmp_u64);
+    for (int64_t i = 0; i < k && i < cap; ++i) {
+        out[2 * i] = (int32_t)(acc[i] >> 32);
+        out[2 * i + 1] = (int32_t)(acc[i] & 0xFFFFFFFFu);
+    }
+    *count = k;
+    free(acc);
+    return ORC_OK;
+}
+
+/*
+ * J of the last batch: its valid updates as (tail, head), insertions oriented after
+ * the batch, deletions before it (Algorithm 5), sorted.
+ */
+int orc_oriented_updates(const orc_plds *h, int32_t *out, int64_t cap, int64_t *count) {
+    if (!h->track || h->last_op < 0) return ORC_EINVAL;
+    const int32_t *lv = h->last_op == 0 ? h->level : h->old_level;
+    uint64_t *acc = (uint64_t *)malloc(sizeof(uint64_t) * (h->last_m > 0 ? h->last_m : 1));
+    if (!acc) return ORC_ENOMEM;
+    for (int64_t i = 0; i < h->last_m; ++i) {
+        int32_t u = (int32_t)(h->last_keys[i] >> 32), v = (int32_t)(h->last_keys[i] & 0xFFFFFFFFu);
+        acc[i] = goes_from(lv, u, v) ? ekey(u, v) : ekey(v, u);
+    }
+    if (h->last_m > 1) qsort(acc, (size_t)h->last_m, sizeof(uint64_t), cmp_u64);
+    for (int64_t i = 0; i < h->last_m && i < cap; ++i) {
+        out[2 * i] = (int32_t)(acc[i] >> 32);
+        out[2 * i + 1] = (int32_t)(acc[i] & 0xFFFFFFFFu);
+    }
+    *count = h->last_m;
+    free(acc);
+    return ORC_OK;
 }

@@ -148,6 +148,10 @@ struct plds {
     DevBuf pool, pool_top, ctl;
     int64_t pool_cap = 0;
     int64_t pool_live = 0;   // slots in use after the last compaction
+    // orientation tracking: levels before the last batch call, its kind, validity
+    DevBuf old_level, oscratch, okeys;
+    int32_t orient_op = -1;
+    bool orient_ok = false;
     int64_t pool_limit = 0;  // bytes a grown pool may take (0: free HBM only)
     // scratch: n-sized
     DevBuf acc, M[2], TL[3], P[2], R, R2, bins, levlist, CL[3];
@@ -223,7 +227,8 @@ static void free_all(plds *h) {
                       &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->inc,   &h->pool,
                       &h->pool_top, &h->ctl, &h->acc,   &h->M[0],  &h->M[1],  &h->TL[0], &h->TL[1], &h->TL[2],
                       &h->P[0],  &h->P[1],  &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0], &h->CL[1],
-                      &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace};
+                      &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace,
+                      &h->old_level, &h->oscratch, &h->okeys};
     for (DevBuf *b : bufs) dev_free(h, *b);
 }
 
@@ -433,8 +438,19 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
     if (B < 0 || (B > 0 && !edges)) return PLDS_EINVAL;
     std::memset(&h->last, 0, sizeof(h->last));
     h->last.submitted = B;
-    if (B == 0) return PLDS_OK;
+    h->orient_ok = false;
     cudaSetDevice(h->device);
+    if (h->tune.track_orientation) {  // levels before the batch, for plds_flips / plds_oriented_updates
+        if (!dev_get(h, h->old_level, 4 * (size_t)h->n)) return PLDS_ENOMEM;
+        cudaMemcpyAsync(h->old_level.p, h->level.p, 4 * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream);
+        h->host_ctl.vcount = 0;
+        h->orient_op = op;
+        if (B == 0) {
+            h->orient_ok = true;
+            return PLDS_OK;
+        }
+    }
+    if (B == 0) return PLDS_OK;
     if (!ensure_batch_scratch(h, B)) return PLDS_ENOMEM;
     const int32_t *dedges = edges;
     if (!is_device_ptr(edges)) {
@@ -498,6 +514,7 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
     h->last.dl_evals = (int64_t)c.st[kStDlEvals];
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
+    h->orient_ok = h->tune.track_orientation != 0;
     return PLDS_OK;
 }
 
@@ -651,6 +668,243 @@ int plds_coreness(plds_t *h, double *out) {
 int plds_coreness_exponent(plds_t *h, int32_t *out) {
     if (!out) return set_status(PLDS_EINVAL);
     return set_status(coreness_impl(h, nullptr, out));
+}
+
+// ---------------------------------------------------------------------------
+// Low out-degree orientation (Section "O(alpha) Out-Degree Orientation",
+// Algorithm 5): an edge goes from the endpoint on the lower level to the one on
+// the higher level, on equal levels from the lower id to the higher id (the
+// reading of Algorithm 5's flip conditions).  Queries on the current levels,
+// and the flipped edges F and oriented updates J of the last batch call made
+// with tuning.track_orientation set (levels saved at its start).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool edge_goes_from(const int32_t *lv, int32_t u, int32_t v) {
+    const int32_t a = lv[u], b = lv[v];
+    return a < b || (a == b && u < v);
+}
+
+__global__ void k_orient(const int32_t *level, const int32_t *slots, const int64_t *off, const int32_t *cap,
+                         int32_t n, const int2 *edges, int64_t B, int32_t *tail) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = edges[i];
+        int32_t t = -1;
+        if (e.x >= 0 && e.x < n && e.y >= 0 && e.y < n && e.x != e.y && table_find(slots, off[e.x], cap[e.x], e.y))
+            t = edge_goes_from(level, e.x, e.y) ? e.x : e.y;
+        tail[i] = t;
+    }
+}
+
+// One warp per vertex: neighbours w with v -> w.
+__global__ void k_out_degrees(const int32_t *level, const int32_t *slots, const int64_t *off, const int32_t *cap,
+                              int32_t n, int32_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
+        const int32_t lv = level[v], c = cap[v];
+        const int4 *t = reinterpret_cast<const int4 *>(slots + off[v]);
+        int cnt = 0;
+        for (int j = lane; j < (c >> 2); j += 32) {
+            const int4 q = t[j];
+            const int32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t w = w4[k];
+                if (w >= 0 && w < n) {
+                    const int32_t lw = level[w];
+                    cnt += (lv < lw || (lv == lw && (int32_t)v < w)) ? 1 : 0;
+                }
+            }
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0) out[v] = cnt;
+    }
+}
+
+__global__ void k_keyset_build(const unsigned long long *keys, int64_t m, unsigned long long *set, int64_t cap) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        uint64_t h = mix64(k) & (uint64_t)(cap - 1);
+        for (int64_t it = 0; it < cap; ++it) {
+            const unsigned long long o = atomicCAS(&set[h], kEmptyKey, k);
+            if (o == kEmptyKey || o == k) break;
+            h = (h + 1) & (uint64_t)(cap - 1);
+        }
+    }
+}
+
+__device__ __forceinline__ bool keyset_has(const unsigned long long *set, int64_t cap, unsigned long long k) {
+    uint64_t h = mix64(k) & (uint64_t)(cap - 1);
+    for (int64_t it = 0; it < cap; ++it) {
+        const unsigned long long o = set[h];
+        if (o == k) return true;
+        if (o == kEmptyKey) return false;
+        h = (h + 1) & (uint64_t)(cap - 1);
+    }
+    return false;
+}
+
+// One warp per vertex whose level changed: its edges whose orientation differs
+// between the saved and the current levels (each edge once: from its lower
+// endpoint among those that moved), minus the edges the batch inserted.
+__global__ void k_flips(const int32_t *level, const int32_t *old_level, const int32_t *slots, const int64_t *off,
+                        const int32_t *cap, int32_t n, const unsigned long long *inserted, int64_t icap, int2 *out,
+                        int64_t out_cap, unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v64 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v64 < n; v64 += nw) {
+        const int32_t v = (int32_t)v64;
+        if (old_level[v] == level[v]) continue;
+        const int32_t c = cap[v];
+        const int4 *t = reinterpret_cast<const int4 *>(slots + off[v]);
+        for (int j = lane; j < (c >> 2); j += 32) {
+            const int4 q = t[j];
+            const int32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t w = w4[k];
+                if (w < 0 || w >= n) continue;
+                if (w < v && old_level[w] != level[w]) continue;
+                const bool b = edge_goes_from(old_level, v, w), a = edge_goes_from(level, v, w);
+                if (a == b) continue;
+                if (icap > 0) {
+                    const unsigned long long key =
+                        ((unsigned long long)(uint32_t)min(v, w) << 32) | (uint32_t)max(v, w);
+                    if (keyset_has(inserted, icap, key)) continue;
+                }
+                const unsigned long long pos = atomicAdd(count, 1ull);
+                if ((int64_t)pos < out_cap) out[pos] = b ? make_int2(v, w) : make_int2(w, v);
+            }
+        }
+    }
+}
+
+__global__ void k_oriented_updates(const unsigned long long *keys, int64_t m, const int32_t *lv, int2 *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = (int32_t)(keys[i] >> 32), v = (int32_t)(keys[i] & 0xffffffffull);
+        out[i] = edge_goes_from(lv, u, v) ? make_int2(u, v) : make_int2(v, u);
+    }
+}
+
+static int orient_grid(const plds *h) { return h->num_sms * 8; }
+
+int plds_orient(plds_t *h, const int32_t *edges, int64_t B, int32_t *tail) {
+    if (!h || B < 0 || (B > 0 && (!edges || !tail))) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    if (B == 0) return set_status(PLDS_OK);
+    cudaSetDevice(h->device);
+    const bool din = is_device_ptr(edges), dout = is_device_ptr(tail);
+    const size_t ebytes = sizeof(int2) * (size_t)B, tbytes = sizeof(int32_t) * (size_t)B;
+    if (!dev_get(h, h->oscratch, (din ? 0 : ebytes) + (dout ? 0 : tbytes) + 16)) return set_status(PLDS_ENOMEM);
+    unsigned char *scr = P<unsigned char>(h->oscratch);
+    const int2 *de = din ? reinterpret_cast<const int2 *>(edges) : reinterpret_cast<const int2 *>(scr);
+    int32_t *dt = dout ? tail : reinterpret_cast<int32_t *>(scr + (din ? 0 : ebytes));
+    if (!din) cudaMemcpyAsync(scr, edges, ebytes, cudaMemcpyHostToDevice, h->stream);
+    k_orient<<<orient_grid(h), 256, 0, h->stream>>>(P<int32_t>(h->level), P<int32_t>(h->pool), P<int64_t>(h->off),
+                                                    P<int32_t>(h->cap), h->n, de, B, dt);
+    h->launches++;
+    if (!dout) cudaMemcpyAsync(tail, dt, tbytes, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return set_status(PLDS_EDEVICE);
+    }
+    return set_status(PLDS_OK);
+}
+
+int plds_out_degrees(plds_t *h, int32_t *out) {
+    if (!h || !out) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    cudaSetDevice(h->device);
+    const bool dout = is_device_ptr(out);
+    if (!dout && !dev_get(h, h->oscratch, 4 * (size_t)h->n)) return set_status(PLDS_ENOMEM);
+    int32_t *d = dout ? out : P<int32_t>(h->oscratch);
+    k_out_degrees<<<orient_grid(h), 256, 0, h->stream>>>(P<int32_t>(h->level), P<int32_t>(h->pool), P<int64_t>(h->off),
+                                                         P<int32_t>(h->cap), h->n, d);
+    h->launches++;
+    if (!dout) cudaMemcpyAsync(out, d, 4 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return set_status(PLDS_EDEVICE);
+    }
+    return set_status(PLDS_OK);
+}
+
+// Copies up to cap pairs of a device list of `total` pairs to out (host or device).
+static int pairs_out(plds *h, int32_t *out, int64_t cap, const void *src, int64_t total) {
+    const int64_t k = std::min(cap, total);
+    if (k > 0 && out) {
+        const size_t bytes = sizeof(int2) * (size_t)k;
+        cudaMemcpyAsync(out, src, bytes, is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return PLDS_EDEVICE;
+    }
+    return PLDS_OK;
+}
+
+int plds_flips(plds_t *h, int32_t *out, int64_t cap, int64_t *count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !out)) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    if (!h->orient_ok) return set_status(PLDS_EINVAL);  // tracking off, or another call since the batch
+    cudaSetDevice(h->device);
+    const int64_t m = (int64_t)h->host_ctl.vcount;
+    int64_t icap = 0;
+    if (h->orient_op == kOpInsert && m > 0) {  // the batch's inserted edges are not flips
+        icap = pow2_at_least(2 * m);
+        if (!dev_get(h, h->okeys, 8 * (size_t)icap)) return set_status(PLDS_ENOMEM);
+        cudaMemsetAsync(h->okeys.p, 0xff, 8 * (size_t)icap, h->stream);
+        k_keyset_build<<<orient_grid(h), 256, 0, h->stream>>>(P<unsigned long long>(h->vkeys), m,
+                                                               P<unsigned long long>(h->okeys), icap);
+        h->launches++;
+    }
+    // count first, then collect into scratch sized by the count
+    int64_t total = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t want = pass == 0 ? 0 : total;
+        if (!dev_get(h, h->oscratch, 8 + sizeof(int2) * (size_t)want + 16)) return set_status(PLDS_ENOMEM);
+        unsigned long long *cnt = P<unsigned long long>(h->oscratch);
+        int2 *lst = reinterpret_cast<int2 *>(P<unsigned char>(h->oscratch) + 16);
+        cudaMemsetAsync(cnt, 0, 8, h->stream);
+        k_flips<<<orient_grid(h), 256, 0, h->stream>>>(P<int32_t>(h->level), P<int32_t>(h->old_level),
+                                                       P<int32_t>(h->pool), P<int64_t>(h->off), P<int32_t>(h->cap),
+                                                       h->n, P<unsigned long long>(h->okeys), icap, lst, want, cnt);
+        h->launches++;
+        unsigned long long c = 0;
+        cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            h->poisoned = true;
+            return set_status(PLDS_EDEVICE);
+        }
+        total = (int64_t)c;
+        if (pass == 1 || total == 0 || cap == 0) break;
+    }
+    *count = total;
+    if (total > 0 && cap > 0) {
+        const int rc = pairs_out(h, out, cap, P<unsigned char>(h->oscratch) + 16, total);
+        if (rc) return set_status(rc);
+    }
+    return set_status(PLDS_OK);
+}
+
+int plds_oriented_updates(plds_t *h, int32_t *out, int64_t cap, int64_t *count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !out)) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    if (!h->orient_ok) return set_status(PLDS_EINVAL);
+    cudaSetDevice(h->device);
+    const int64_t m = (int64_t)h->host_ctl.vcount;
+    *count = m;
+    if (m == 0 || cap == 0) return set_status(PLDS_OK);
+    if (!dev_get(h, h->oscratch, sizeof(int2) * (size_t)m + 16)) return set_status(PLDS_ENOMEM);
+    int2 *lst = reinterpret_cast<int2 *>(P<unsigned char>(h->oscratch));
+    const int32_t *lv = h->orient_op == kOpInsert ? P<int32_t>(h->level) : P<int32_t>(h->old_level);
+    k_oriented_updates<<<orient_grid(h), 256, 0, h->stream>>>(P<unsigned long long>(h->vkeys), m, lv, lst);
+    h->launches++;
+    return set_status(pairs_out(h, out, cap, lst, m));
 }
 
 int plds_levels(plds_t *h, int32_t *out) {
@@ -812,6 +1066,7 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     if (h->poisoned) return set_status(PLDS_EPOISONED);
     std::memset(&h->last, 0, sizeof(h->last));
     h->last.submitted = B;
+    h->orient_ok = false;
     if (B == 0) return set_status(PLDS_OK);
     if (cudaSetDevice(h->device) != cudaSuccess) {
         cudaGetLastError();
@@ -1074,8 +1329,10 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
     if (offsets[0] != 0 || total < 0 || (total > 0 && !edges)) return set_status(PLDS_EINVAL);
     for (int32_t k = 0; k < 2 * G; ++k)
         if (offsets[k + 1] < offsets[k]) return set_status(PLDS_EINVAL);
-    for (plds *h : s->g)
+    for (plds *h : s->g) {
         if (h->poisoned) return set_status(PLDS_EPOISONED);
+        h->orient_ok = false;
+    }
     plds *o = s->owner;
     cudaSetDevice(o->device);
     const int32_t *dedges = edges;
@@ -1791,6 +2048,7 @@ extern "C" int plds_server_submit(plds_server_t *sv, int32_t op, const int32_t *
     if (op == kReqCoreness && !out) return set_status(PLDS_EINVAL);
     plds *h = sv->h;
     if (h->poisoned) return set_status(PLDS_EPOISONED);
+    h->orient_ok = false;
     cudaSetDevice(h->device);
     // wait for a free slot (collect finished requests, keep the loop alive)
     const auto t0 = std::chrono::steady_clock::now();

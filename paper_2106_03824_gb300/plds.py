@@ -47,7 +47,7 @@ class PldsTuning(ctypes.Structure):
                 ("load_den", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("test_delay_us", ctypes.c_int32),
                 ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32),
-                ("block_cap", ctypes.c_int32)]
+                ("block_cap", ctypes.c_int32), ("track_orientation", ctypes.c_int32)]
 
     KNOBS = ("thread_max_cap", "block_cap", "load_num", "load_den")
 
@@ -121,6 +121,10 @@ def load():
     L.plds_server_destroy.restype = None
     L.plds_server_configure.argtypes = [vp, i64, i64]
     L.plds_server_admission.argtypes = [i64, i64, i64, i64, i64]
+    L.plds_orient.argtypes = [vp, vp, i64, vp]
+    L.plds_out_degrees.argtypes = [vp, vp]
+    L.plds_flips.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
+    L.plds_oriented_updates.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
     L.plds_opt_levels_per_group.argtypes = [i64, dbl]
     L.plds_opt_levels_per_group.restype = i32
     L.plds_last_status.argtypes = []
@@ -271,6 +275,35 @@ class PLDS:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(load().plds_set_tuning(self._h, ctypes.byref(t)), "plds_set_tuning")
+
+    # orientation (Algorithm 5)
+    def orient(self, edges) -> np.ndarray:
+        """Tail (source endpoint) of each edge, -1 if absent or invalid."""
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2) if isinstance(edges, np.ndarray) \
+            else edges
+        out = np.zeros(e.shape[0], np.int32)
+        self._check(load().plds_orient(self._h, _ptr(e), int(e.shape[0]), _ptr(out)), "plds_orient")
+        return out
+
+    def out_degrees(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        self._check(load().plds_out_degrees(self._h, _ptr(out)), "plds_out_degrees")
+        return out
+
+    def _pairs(self, fn, name) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        self._check(fn(self._h, None, 0, ctypes.byref(cnt)), name)
+        out = np.zeros((max(cnt.value, 1), 2), np.int32)
+        self._check(fn(self._h, _ptr(out), cnt.value, ctypes.byref(cnt)), name)
+        return out[:cnt.value]
+
+    def flips(self) -> np.ndarray:
+        """F of the last tracked batch call: (tail, head) before the flip, unordered."""
+        return self._pairs(load().plds_flips, "plds_flips")
+
+    def oriented_updates(self) -> np.ndarray:
+        """J of the last tracked batch call, unordered."""
+        return self._pairs(load().plds_oriented_updates, "plds_oriented_updates")
 
     def trace(self, cap: int = 1 << 16):
         out = np.zeros((cap, 12), np.int32)

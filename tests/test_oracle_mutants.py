@@ -40,6 +40,12 @@ MUTANTS = {
     # preprocessing keeps already-present edges
     "no_presence_filter": ("if (has_edge(h, u, v) != want_present) { h->st_filtered++; continue; }",
                            "if (0) { h->st_filtered++; continue; }"),
+    # orientation ties broken from the higher id to the lower id
+    "orient_tie": ("return lv[u] < lv[v] || (lv[u] == lv[v] && u < v);",
+                   "return lv[u] < lv[v] || (lv[u] == lv[v] && u > v);"),
+    # flips of the last batch compared against the levels after it on both sides
+    "flips_no_snapshot": ("int before = goes_from(h->old_level, u, v), after = goes_from(h->level, u, v);",
+                          "int before = goes_from(h->level, u, v), after = goes_from(h->level, u, v);"),
     # levels per group 4t replaced by t
     "group_size": ("T->Lg = lg_override > 0 ? lg_override : 4 * (t > 1 ? t : 1);",
                    "T->Lg = lg_override > 0 ? lg_override : (t > 1 ? t : 1);"),

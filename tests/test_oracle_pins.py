@@ -404,3 +404,71 @@ def test_opt_levels_per_group_against_logarithms():
         assert O.opt_levels_per_group(m, d) == max(1, math.ceil(x)), (m, d)
         checked += 1
     assert checked > 350
+
+
+# ----------------------------------------------------------------------------
+# Low out-degree orientation (Section "O(alpha) Out-Degree Orientation", Algorithm 5)
+# ----------------------------------------------------------------------------
+
+def test_orientation_hand_example():
+    """Triangle 0-1-2 plus edge 2-3, levels 3, 1, 1, 1: edges go from the lower level
+    to the higher one, and on equal levels from the lower id to the higher id
+    (Algorithm 5's flip conditions keep H[(u,v)] = 0, u < v, when levels are equal)."""
+    h = O.OraclePLDS(4, 1.0, 3.0, levels_per_group=3)
+    h.add_edges_raw([(0, 1), (1, 2), (0, 2), (2, 3)])
+    for v, l in ((0, 3), (1, 1), (2, 1), (3, 1)):
+        h.set_level(v, l)
+    tails = h.orient([(0, 1), (1, 2), (0, 2), (2, 3), (3, 2), (0, 3), (1, 1), (0, 9)])
+    assert list(tails) == [1, 1, 2, 2, 2, -1, -1, -1]
+    assert list(h.out_degrees()) == [0, 2, 2, 0]
+
+
+def _key_order(levels, u, v):
+    return (levels[u], u) < (levels[v], v)
+
+
+def test_orientation_acyclic_bounded_and_flips_by_brute_force():
+    """On random batch sequences: every edge goes up the (level, id) order (so the
+    orientation is acyclic), out-degree <= up-degree <= the level's Invariant-1
+    cutoff, and F / J equal a brute-force comparison of the level arrays and edge
+    sets before and after each batch."""
+    rng = np.random.default_rng(21)
+    n = 60
+    allp = _ref.all_pairs(n)
+    for trial in range(6):
+        h = O.OraclePLDS(n)
+        h.track(True)
+        T = O.tables(n)
+        present = set()
+        for step in range(10):
+            before_lv = h.levels().copy()
+            before_e = set(map(tuple, h.edges().tolist()))
+            if rng.random() < 0.6 or not present:
+                pick = [allp[i] for i in rng.choice(len(allp), size=int(rng.integers(1, 120)), replace=False)]
+                h.insert(pick)
+                op = 0
+            else:
+                cur = sorted(present)
+                pick = [cur[i] for i in rng.choice(len(cur), size=int(rng.integers(1, len(cur) + 1)), replace=False)]
+                h.delete(pick)
+                op = 1
+            lv = h.levels()
+            after_e = set(map(tuple, h.edges().tolist()))
+            present = after_e
+            deg, up, _ = h.counters()
+            out = h.out_degrees()
+            for (u, v) in after_e:
+                t = h.orient([(u, v)])[0]
+                assert t == (u if _key_order(lv, u, v) else v)
+            assert np.all(out <= up)
+            assert np.all(out <= np.asarray(T["upmax"])[lv // T["Lg"]])
+            assert out.sum() == len(after_e)
+            expect_f = sorted((u, v) if _key_order(before_lv, u, v) else (v, u)
+                              for (u, v) in (before_e & after_e)
+                              if _key_order(before_lv, u, v) != _key_order(lv, u, v))
+            assert [tuple(x) for x in h.flips().tolist()] == expect_f
+            changed = (after_e - before_e) if op == 0 else (before_e - after_e)
+            ref_lv = lv if op == 0 else before_lv
+            expect_j = sorted((u, v) if _key_order(ref_lv, u, v) else (v, u) for (u, v) in changed)
+            assert [tuple(x) for x in h.oriented_updates().tolist()] == expect_j
+        h.close()
