@@ -105,8 +105,12 @@ plds_t *plds_create(int32_t n, double delta, double lambda);
 /*
  * As plds_create, plus: levels_per_group (0 = the paper's 4*ceil(log_{1+delta} n);
  * a positive value overrides it), allocator (NULL = cudaMallocAsync/cudaFreeAsync),
- * stream (a cudaStream_t; NULL = the legacy default stream), flags (must be 0).
+ * stream (a cudaStream_t; NULL = the legacy default stream), flags (0, or
+ * PLDS_FLAG_HEURISTIC: Invariant 1's coefficient 2 + 3/lambda replaced by 1.1, the
+ * experiments section's "heuristic parameters" -- both invariants still hold, the
+ * efficiency and approximation bounds do not; other bits: PLDS_EINVAL).
  */
+#define PLDS_FLAG_HEURISTIC 1u
 plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
                        const plds_allocator *allocator, void *stream, uint32_t flags);
 

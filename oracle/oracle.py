@@ -48,6 +48,9 @@ def lib():
         i32p = ctypes.POINTER(ctypes.c_int32)
         L.orc_create.restype = P
         L.orc_create.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
+        L.orc_create_ex.restype = P
+        L.orc_create_ex.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                    ctypes.c_int32]
         L.orc_destroy.argtypes = [P]
         for name in ("orc_insert", "orc_delete", "orc_add_edges_raw"):
             getattr(L, name).argtypes = [P, P, ctypes.c_int64]
@@ -58,7 +61,7 @@ def lib():
         L.orc_counters.argtypes = [P, P, P, P]
         L.orc_check.argtypes = [P]
         L.orc_set_level.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
-        L.orc_tables_query.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+        L.orc_tables_query.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, P, P,
                                        ctypes.c_int32]
         L.orc_exact_coreness.argtypes = [ctypes.c_int32, P, ctypes.c_int64, P]
@@ -90,14 +93,17 @@ def opt_levels_per_group(m: int, delta: float = 0.4) -> int:
     return r
 
 
-def tables(n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0):
+HEURISTIC = 1  # Invariant 1's coefficient 2 + 3/lambda replaced by 1.1
+
+
+def tables(n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0, flags: int = 0):
     """Exact (t, Lg, G, K, upmax[G], dnmin[G]) from the oracle's rational arithmetic."""
     L = lib()
     t, Lg, G, K = (ctypes.c_int32() for _ in range(4))
     cap = 8192
     up = np.zeros(cap, np.int32)
     dn = np.zeros(cap, np.int32)
-    rc = L.orc_tables_query(n, delta, lam, levels_per_group, ctypes.byref(t), ctypes.byref(Lg),
+    rc = L.orc_tables_query(n, delta, lam, levels_per_group, flags, ctypes.byref(t), ctypes.byref(Lg),
                             ctypes.byref(G), ctypes.byref(K), _ptr(up), _ptr(dn), cap)
     if rc != ORC_OK:
         raise ValueError(f"orc_tables_query rc={rc}")
@@ -122,9 +128,10 @@ STAT_KEYS = ("submitted", "self_loops", "duplicates", "filtered", "valid", "roun
 class OraclePLDS:
     """Sequential PLDS; one instance per graph."""
 
-    def __init__(self, n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0):
+    def __init__(self, n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0,
+                 flags: int = 0):
         self.n = n
-        self._h = lib().orc_create(n, delta, lam, levels_per_group)
+        self._h = lib().orc_create_ex(n, delta, lam, levels_per_group, flags)
         if not self._h:
             raise ValueError("orc_create failed (bad n / delta / lambda)")
         p = np.zeros(4, np.int32)

@@ -180,12 +180,17 @@ typedef struct {
  * Group count and per-group thresholds (Invariants 1 and 2; group size from the
  * "Detailed PLDS Algorithm" section and the coreness-estimate Definition).
  */
-static int build_tables(orc_tables *T, int32_t n, double delta, double lambda, int32_t lg_override) {
+/* flags: ORC_HEURISTIC replaces Invariant 1's coefficient 2 + 3/lambda by 1.1, the
+   experiments' "heuristic parameters" (their efficiency bounds no longer hold). */
+#define ORC_HEURISTIC 1
+
+static int build_tables(orc_tables *T, int32_t n, double delta, double lambda, int32_t lg_override,
+                        int32_t flags) {
     memset(T, 0, sizeof(*T));
     if (n < 1) return ORC_EINVAL;
     if (to_rational(delta, &T->dnum, &T->dden)) return ORC_EINVAL;
     if (to_rational(lambda, &T->lnum, &T->lden)) return ORC_EINVAL;
-    if (lg_override < 0) return ORC_EINVAL;
+    if (lg_override < 0 || (flags & ~ORC_HEURISTIC)) return ORC_EINVAL;
     T->n = n;
     int err = 0;
     /* t: smallest t with (dden+dnum)^t >= n * dden^t */
@@ -210,15 +215,20 @@ static int build_tables(orc_tables *T, int32_t n, double delta, double lambda, i
     T->upmax = (int32_t *)malloc(sizeof(int32_t) * T->G);
     T->dnmin = (int32_t *)malloc(sizeof(int32_t) * T->G);
     if (!T->upmax || !T->dnmin) return ORC_ENOMEM;
-    /* (2 + 3/lambda) = (2*lnum + 3*lden)/lnum ; (1+delta)^i = (dden+dnum)^i / dden^i */
+    /* (2 + 3/lambda) = (2*lnum + 3*lden)/lnum, or 11/10 ; (1+delta)^i = (dden+dnum)^i / dden^i */
+    uint64_t cnum = (uint64_t)(2 * T->lnum + 3 * T->lden), cden = (uint64_t)T->lnum;
+    if (flags & ORC_HEURISTIC) {
+        cnum = 11;
+        cden = 10;
+    }
     static bignum num, den, pw, qw;
     bn_from(&pw, 1);
     bn_from(&qw, 1);
     for (int i = 0; i < T->G; ++i) {
         num = pw;
-        if (bn_mul_small(&num, (uint64_t)(2 * T->lnum + 3 * T->lden))) return ORC_EINVAL;
+        if (bn_mul_small(&num, cnum)) return ORC_EINVAL;
         den = qw;
-        if (bn_mul_small(&den, (uint64_t)T->lnum)) return ORC_EINVAL;
+        if (bn_mul_small(&den, cden)) return ORC_EINVAL;
         T->upmax[i] = (int32_t)bn_floor_div_clamped(&num, &den, n, &err);
         T->dnmin[i] = (int32_t)bn_ceil_div_clamped(&pw, &qw, n, &err);
         if (err) return ORC_EINVAL;
@@ -433,11 +443,11 @@ static int32_t desire_level(orc_plds *h, int32_t v, int32_t *hist) {
 /* ------------------------------------------------------------------------- */
 void orc_destroy(orc_plds *h);
 
-int orc_tables_query(int32_t n, double delta, double lambda, int32_t lg_override,
+int orc_tables_query(int32_t n, double delta, double lambda, int32_t lg_override, int32_t flags,
                      int32_t *out_t, int32_t *out_Lg, int32_t *out_G, int32_t *out_K,
                      int32_t *upmax, int32_t *dnmin, int32_t cap) {
     orc_tables T;
-    int rc = build_tables(&T, n, delta, lambda, lg_override);
+    int rc = build_tables(&T, n, delta, lambda, lg_override, flags);
     if (rc == ORC_OK) {
         *out_t = T.t;
         *out_Lg = T.Lg;
@@ -453,10 +463,10 @@ int orc_tables_query(int32_t n, double delta, double lambda, int32_t lg_override
     return rc;
 }
 
-orc_plds *orc_create(int32_t n, double delta, double lambda, int32_t lg_override) {
+orc_plds *orc_create_ex(int32_t n, double delta, double lambda, int32_t lg_override, int32_t flags) {
     orc_plds *h = (orc_plds *)calloc(1, sizeof(orc_plds));
     if (!h) return NULL;
-    if (build_tables(&h->T, n, delta, lambda, lg_override) != ORC_OK) {
+    if (build_tables(&h->T, n, delta, lambda, lg_override, flags) != ORC_OK) {
         free(h->T.upmax);
         free(h->T.dnmin);
         free(h);
@@ -479,6 +489,10 @@ orc_plds *orc_create(int32_t n, double delta, double lambda, int32_t lg_override
     for (int32_t i = 0; i < n; ++i) h->dl[i] = -1;
     h->last_op = -1;
     return h;
+}
+
+orc_plds *orc_create(int32_t n, double delta, double lambda, int32_t lg_override) {
+    return orc_create_ex(n, delta, lambda, lg_override, 0);
 }
 
 void orc_destroy(orc_plds *h) {

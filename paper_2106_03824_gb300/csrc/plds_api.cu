@@ -525,7 +525,7 @@ extern "C" {
 
 plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
                        const plds_allocator *allocator, void *stream, uint32_t flags) {
-    if (flags != 0 || (allocator && (!allocator->alloc || !allocator->free))) {
+    if ((flags & ~(uint32_t)PLDS_FLAG_HEURISTIC) != 0 || (allocator && (!allocator->alloc || !allocator->free))) {
         set_status(PLDS_EINVAL);
         return nullptr;
     }
@@ -534,7 +534,7 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
         set_status(PLDS_ENOMEM);
         return nullptr;
     }
-    if (build_tables(n, delta, lambda, levels_per_group, &h->T) != 0) {
+    if (build_tables(n, delta, lambda, levels_per_group, &h->T, (flags & PLDS_FLAG_HEURISTIC) != 0) != 0) {
         delete h;
         set_status(PLDS_EINVAL);
         return nullptr;

@@ -97,7 +97,7 @@ int64_t divide(const Nat &x, const Nat &y, bool *exact) {
 
 }  // namespace
 
-int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_group, Tables *out) {
+int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_group, Tables *out, bool heuristic) {
     if (n < 1 || !(delta > 0) || !(lambda > 0) || delta > 1e6 || lambda > 1e6 || levels_per_group < 0) return -1;
     int64_t p = std::llround(delta * 1e6), q = 1000000, a = std::llround(lambda * 1e6), b = 1000000;
     if (p <= 0 || a <= 0) return -1;
@@ -120,11 +120,12 @@ int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_grou
     out->K = (int32_t)K;
     out->upmax.assign(out->G, 0);
     out->dnmin.assign(out->G, 0);
-    // c = (2a + 3b) / a ; (1+delta)^i = (q+p)^i / q^i
+    // c = (2a + 3b) / a, or 11/10 for the heuristic ; (1+delta)^i = (q+p)^i / q^i
+    const uint32_t cn = heuristic ? 11u : (uint32_t)(2 * a + 3 * b), cd = heuristic ? 10u : (uint32_t)a;
     Nat pw = Nat::of(1), qw = Nat::of(1);
     for (int i = 0; i < out->G; ++i) {
-        Nat x = mul(pw, (uint32_t)(2 * a + 3 * b));
-        Nat y = mul(qw, (uint32_t)a);
+        Nat x = mul(pw, cn);
+        Nat y = mul(qw, cd);
         bool exact;
         // clamp: x >= n*y  <=>  floor(x/y) >= n
         if (cmp(x, mul(y, (uint32_t)n)) >= 0) out->upmax[i] = n;

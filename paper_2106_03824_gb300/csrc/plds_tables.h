@@ -17,7 +17,9 @@ struct Tables {
 
 // 0 on success, -1 on invalid parameters (n < 1, delta/lambda not positive,
 // more than 512 groups or 2^24 levels).
-int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_group, Tables *out);
+// heuristic: Invariant 1's coefficient 2 + 3/lambda replaced by 1.1.
+int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_group, Tables *out,
+                 bool heuristic = false);
 
 // Levels per group of the optimised variant: ceil(log_{1+delta}(m) / 50), at least 1
 // (the smallest L >= 1 with (1+delta)^(50 L) >= m, exact).  -1 on invalid input

@@ -188,6 +188,34 @@ def test_rmat_every_batch(P, scale, batch):
     g.close()
 
 
+@pytest.mark.parametrize("delta,lam,heuristic", [(0.2, 12.0, False), (0.8, 6.0, False), (1.6, 48.0, False),
+                                                  (3.2, 96.0, False), (6.4, 24.0, False), (0.4, 3.0, True),
+                                                  (1.6, 3.0, True)])
+def test_parameter_grid_every_batch(P, delta, lam, heuristic):
+    """Other points of the experiments' delta / lambda grid, and the heuristic
+    coefficient 1.1: Chung-Lu n = 5000, Ins then Del batches, equal to the oracle
+    after every batch (tables included)."""
+    n = 5000
+    e = W.chung_lu(n, 30_000, 2.3, seed=31)
+    flags = O.HEURISTIC if heuristic else 0
+    g = P.PLDS(n, delta, lam, heuristic=heuristic)
+    o = O.OraclePLDS(n, delta, lam, flags=flags)
+    T = O.tables(n, delta, lam, flags=flags)
+    up, dn = g.tables()
+    assert np.array_equal(up, T["upmax"]) and np.array_equal(dn, T["dnmin"])
+    for i, b in enumerate(W.batches(W.shuffled(e, 3), 4000)):
+        g.insert(b)
+        o.insert(b)
+        assert_same(g, o, f"ins {i}")
+        assert_stats(g, o, f"ins {i}")
+    for i, b in enumerate(W.batches(W.shuffled(e, 4), 4000)):
+        g.delete(b)
+        o.delete(b)
+        assert_same(g, o, f"del {i}")
+        assert_stats(g, o, f"del {i}")
+    g.close()
+
+
 def test_pldsopt_every_batch(P):
     """PLDSOpt (ceil(log_{1+delta} m / 50) levels per group, here 1): the same batch
     rules on fewer levels; levels, counters and work counts equal the oracle's with

@@ -472,3 +472,23 @@ def test_orientation_acyclic_bounded_and_flips_by_brute_force():
             expect_j = sorted((u, v) if _key_order(ref_lv, u, v) else (v, u) for (u, v) in changed)
             assert [tuple(x) for x in h.oriented_updates().tolist()] == expect_j
         h.close()
+
+
+def test_heuristic_coefficient_tables():
+    """Heuristic parameters (experiments section): 2 + 3/lambda replaced by 1.1, so
+    upmax[i] = floor(1.1 * 1.4^i): 1, 1, 2, 3, 4, 5 (1.1 * 1.4^5 = 5.916...), and the
+    Invariant-2 side is unchanged."""
+    T = O.tables(1000, 0.4, 3.0, flags=O.HEURISTIC)
+    assert list(T["upmax"][:6]) == [1, 1, 2, 3, 4, 5]
+    assert list(T["dnmin"]) == list(O.tables(1000, 0.4, 3.0)["dnmin"])
+    # lambda plays no part any more
+    assert list(T["upmax"]) == list(O.tables(1000, 0.4, 96.0, flags=O.HEURISTIC)["upmax"])
+    # the invariants still hold after every batch
+    e = W.chung_lu(2000, 12_000, 2.3, seed=4)
+    h = O.OraclePLDS(2000, flags=O.HEURISTIC)
+    for b in W.batches(W.shuffled(e, 1), 3000):
+        assert h.insert(b) == 0
+        assert h.check() == 0
+    for b in W.batches(W.shuffled(e, 2), 3000):
+        assert h.delete(b) == 0
+        assert h.check() == 0
