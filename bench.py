@@ -250,6 +250,133 @@ def make_batched(graphs: int, rounds: int, seed: int = 7):
     return ns, pre, rnds
 
 
+def device_checks(P, g, n, present, tables):
+    """Counters by definition and Invariants 1-2 computed on the device with torch
+    (graphs too large for the host check): deg, up (neighbours on the same level or
+    above) and up* (on the level below or above) recounted from the edge list and
+    the levels, compared with the structure's own counters."""
+    import torch
+    dev = present.device
+    lv = torch.empty(n, dtype=torch.int32, device=dev)
+    g.levels(lv)
+    mine = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(3)]
+    g.counters(mine)
+    torch.cuda.synchronize()
+    lv = lv.long()
+    deg, up, ups = (torch.zeros(n, dtype=torch.int64, device=dev) for _ in range(3))
+    chunk = 1 << 26
+    for s0 in range(0, present.shape[0], chunk):
+        u = present[s0:s0 + chunk, 0].long()
+        v = present[s0:s0 + chunk, 1].long()
+        lu, lw = lv[u], lv[v]
+        one = torch.ones_like(u)
+        deg.index_add_(0, u, one)
+        deg.index_add_(0, v, one)
+        up.index_add_(0, u, (lw >= lu).long())
+        up.index_add_(0, v, (lu >= lw).long())
+        ups.index_add_(0, u, (lw >= lu - 1).long())
+        ups.index_add_(0, v, (lu >= lw - 1).long())
+    upmax = torch.as_tensor(np.asarray(tables[0], np.int64), device=dev)
+    dnmin = torch.as_tensor(np.asarray(tables[1], np.int64), device=dev)
+    Lg = g.Lg
+    pos = lv > 0
+    return {"deg_by_definition": bool(torch.equal(deg, mine[0].long())),
+            "up_by_definition": bool(torch.equal(up, mine[1].long())),
+            "upstar_by_definition": bool(torch.equal(ups, mine[2].long())),
+            "invariant1": bool((up <= upmax[lv // Lg]).all()),
+            "invariant2": bool((ups[pos] >= dnmin[(lv[pos] - 1) // Lg]).all())}
+
+
+def run_large(args):
+    """The large configuration: a Chung-Lu graph shaped like a billion-edge social
+    graph (n = 41.7M, ~1.2B edges, exponent 2.1) and a 24M-vertex road-like grid,
+    plain form, device-resident inputs; Ins / Mix / Del protocols at batches of 1e7
+    and 1e6, device-side property checks on the loaded graph."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_03824_gb300 import plds as P
+    torch.cuda.set_device(0)
+    n, m = args.large_n, args.large_m
+    t0 = time.perf_counter()
+    e = W.shuffled_device(W.chung_lu_device(n, m, 2.1, seed=1), 11)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    m = int(e.shape[0])
+
+    def timed(calls):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+        upd = 0
+        torch.cuda.synchronize()
+        evs[0].record()
+        for i, (fn, b) in enumerate(calls):
+            fn(b)
+            upd += b.shape[0]
+            evs[i + 1].record()
+        torch.cuda.synchronize()
+        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(calls))]
+        return {"updates_per_s": upd / (evs[0].elapsed_time(evs[-1]) / 1e3), "batches": len(calls),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    out = {}
+    g = P.PLDS(n)
+    k = int(0.9 * m)
+    B7, B6 = 10_000_000, 1_000_000
+    # build: the first 90 % in batches of 1e7 (the Ins protocol at 1e7)
+    out["ins_1e7"] = timed([(g.insert, e[s:min(s + B7, k)]) for s in range(0, k, B7)])
+    st = g.stats()
+    out["loaded"] = {"edges": k, "device_bytes": st["device_bytes"], "pool_slots": st["pool_slots_cap"]}
+    out["checks_loaded"] = device_checks(P, g, n, e[:k], g.tables())
+    # Mix on the 90 %-loaded graph: insert from the absent 10 %, delete from a shuffled present pool
+    present = W.shuffled_device(e[:k], 12)
+    ai, pi = k, 0
+
+    def mixed(B, count):
+        nonlocal ai, pi
+        calls = []
+        for _ in range(count):
+            h = B // 2
+            calls.append((g.insert, e[ai:ai + h]))
+            calls.append((g.delete, present[pi:pi + h]))
+            ai += h
+            pi += h
+        return calls
+
+    out["mix_1e7"] = timed(mixed(B7, 3))
+    out["mix_1e6"] = timed(mixed(B6, 10))
+    out["ins_1e6"] = timed([(g.insert, e[ai + j * B6:ai + (j + 1) * B6]) for j in range(5)])
+    ai += 5 * B6
+    out["del_1e6"] = timed([(g.delete, present[pi + j * B6:pi + (j + 1) * B6]) for j in range(5)])
+    pi += 5 * B6
+    # Del at 1e7: everything still present
+    rest = torch.cat([present[pi:], e[k:ai]])
+    out["del_1e7"] = timed([(g.delete, rest[s:s + B7]) for s in range(0, rest.shape[0], B7)])
+    out["empty_after_del"] = bool(int(g.levels().max()) == 0 and int(g.counters()[0].max()) == 0)
+    g.close()
+    del e, present, rest
+    torch.cuda.empty_cache()
+    # the road-like contrast: 24M-vertex grid, degree <= 4 plus 10 % diagonals
+    side = args.grid_side
+    ge = torch.from_numpy(W.shuffled(W.grid2d(side, 0.1, seed=1), 13)).cuda()
+    ng = side * side
+    g = P.PLDS(ng)
+    grid = {"n": ng, "m": int(ge.shape[0])}
+    grid["ins_1e7"] = timed([(g.insert, ge[s:s + B7]) for s in range(0, ge.shape[0], B7)])
+    grid["checks_loaded"] = device_checks(P, g, ng, ge, g.tables())
+    grid["max_level"] = int(g.levels().max())
+    gd = W.shuffled_device(ge, 14)
+    grid["del_1e7"] = timed([(g.delete, gd[s:s + B7]) for s in range(0, gd.shape[0], B7)])
+    g.close()
+    line = {"metric": "edge updates/s, large graphs (plain form)", "value": out["ins_1e7"]["updates_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": out["ins_1e7"]["batches"], "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "form": "large",
+            "config": {"workload": f"Chung-Lu n={n}, m={m}, exponent 2.1 (generated on the device, "
+                                   f"{t_gen:.1f} s); grid {side}x{side} with 10% diagonals",
+                       "value_is": "Ins protocol at batch 1e7 while loading 90% of the edges"},
+            "chung_lu": out, "grid": grid}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     import torch
     import __graft_entry__
@@ -497,7 +624,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-protocols", action="store_true")
     ap.add_argument("--dump-recs", default=None, help="write per-step kernel records (JSON) to this path")
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving", "large"])
+    ap.add_argument("--large-n", type=int, default=41_700_000)
+    ap.add_argument("--large-m", type=int, default=1_200_000_000)
+    ap.add_argument("--grid-side", type=int, default=4899)
     ap.add_argument("--serve-n", type=int, default=4_800_000)
     ap.add_argument("--serve-m", type=int, default=43_000_000)
     ap.add_argument("--requests", type=int, default=400)
@@ -514,6 +644,8 @@ def main():
         return run_batched(args)
     if args.form == "serving":
         return run_serving(args)
+    if args.form == "large":
+        return run_large(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

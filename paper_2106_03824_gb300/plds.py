@@ -256,8 +256,9 @@ class PLDS:
         self._check(load().plds_levels(self._h, _ptr(out)), "plds_levels")
         return out
 
-    def counters(self):
-        d, u, s = (np.zeros(self.n, np.int32) for _ in range(3))
+    def counters(self, out=None):
+        """(deg, up, up*); out = three preallocated int32 buffers (host or device) or None."""
+        d, u, s = out if out is not None else (np.zeros(self.n, np.int32) for _ in range(3))
         self._check(load().plds_counters(self._h, _ptr(d), _ptr(u), _ptr(s)), "plds_counters")
         return d, u, s
 
