@@ -219,6 +219,22 @@ int plds_out_degrees(plds_t *h, int32_t *out);
 int plds_flips(plds_t *h, int32_t *out, int64_t cap, int64_t *count);
 int plds_oriented_updates(plds_t *h, int32_t *out, int64_t cap, int64_t *count);
 
+/*
+ * Static (2+eps')-approximate k-core (Section "Static (2+eps)-Approximate k-Core",
+ * Algorithm 6) of the handle's current graph; the levels are not touched.
+ * Bucketed peeling with eps = (sqrt(4 eps' + 9) - 3) / 2 and delta = 2 / eps:
+ * C[v] starts at deg(v), bucket(C) = ceil(log_{1+eps} C) (decided against the
+ * table (1+eps)^b built by repeated multiplication in double); the outer loop takes
+ * the lowest non-empty bucket as threshold index t; up to ceil(log_{1+delta} n)
+ * inner iterations each peel the whole lowest bucket and set every surviving
+ * neighbour's C = max(C - r, ceil((1+eps)^(t-1))) (r = its peeled neighbours) and
+ * bucket = max(bucket(C), t), continuing while (1+eps)^next <= (2+eps)(1+eps)^t.
+ * out[v] = (1+eps)^(v's bucket when peeled), 0 for isolated vertices (the worked
+ * example's values); double[n], host or device.  stats (int64[3] or NULL): outer
+ * iterations, inner iterations, neighbour visits.  PLDS_EINVAL for eps' <= 0.
+ */
+int plds_static_coreness(plds_t *h, double eps_prime, double *out, int64_t *stats);
+
 /* Use another stream for subsequent calls. */
 int plds_set_stream(plds_t *h, void *stream);
 

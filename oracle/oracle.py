@@ -30,8 +30,10 @@ def build(force: bool = False) -> Path:
     _OUT.parent.mkdir(parents=True, exist_ok=True)
     if force or not _OUT.exists() or _OUT.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _OUT.with_suffix(f".{os.getpid()}.tmp.so")
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-Wall", "-shared", "-fPIC",
-                               "-o", str(tmp), str(_SRC)])
+        # no fused multiply-add contraction: the static k-core's double thresholds must
+        # round the same way on every host
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-Wall", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-o", str(tmp), str(_SRC), "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -71,6 +73,10 @@ def lib():
         for name in ("orc_flips", "orc_oriented_updates"):
             getattr(L, name).argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.orc_opt_levels_per_group.argtypes = [ctypes.c_int64, ctypes.c_double]
+        L.orc_static_coreness.argtypes = [P, ctypes.c_double, P, P]
+        L.orc_static_thresholds.argtypes = [ctypes.c_int32, ctypes.c_double, P, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]
+        L.orc_static_thresholds.restype = ctypes.c_int32
         L.orc_opt_levels_per_group.restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -232,3 +238,23 @@ class OraclePLDS:
     def oriented_updates(self) -> np.ndarray:
         """The last batch's valid updates oriented as Algorithm 5 returns them, sorted."""
         return self._pairs(lib().orc_oriented_updates)
+
+    # static (2+eps')-approximate k-core (Algorithm 6)
+    def static_coreness(self, eps_prime: float = 1.0):
+        """(estimates, {outer, inner, visits}) of Algorithm 6 on the current graph."""
+        est = np.zeros(self.n, np.float64)
+        st = np.zeros(3, np.int64)
+        rc = lib().orc_static_coreness(self._h, float(eps_prime), _ptr(est), _ptr(st))
+        if rc != ORC_OK:
+            raise ValueError(f"orc_static_coreness rc={rc}")
+        return est, dict(outer=int(st[0]), inner=int(st[1]), visits=int(st[2]))
+
+
+def static_thresholds(n: int, eps_prime: float = 1.0):
+    """(thresholds (1+eps)^b, J) of Algorithm 6 for n vertices."""
+    thr = np.zeros(4096, np.float64)
+    J = ctypes.c_int32()
+    k = lib().orc_static_thresholds(int(n), float(eps_prime), _ptr(thr), 4096, ctypes.byref(J))
+    if k < 0:
+        raise ValueError(f"orc_static_thresholds rc={k}")
+    return thr[:k].copy(), J.value

@@ -37,6 +37,7 @@
  * definition by scanning the neighbour list, which is slow but leaves nothing to
  * keep in sync.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1079,4 +1080,141 @@ int orc_oriented_updates(const orc_plds *h, int32_t *out, int64_t cap, int64_t *
     *count = h->last_m;
     free(acc);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Static (2+eps')-approximate k-core (Section "Static (2+eps)-Approximate    */
+/* k-Core", Algorithm 6): bucketed peeling with thresholds (1+eps)^b.         */
+/*                                                                           */
+/* Readings (listed in the design notes):                                    */
+/*  - eps = (sqrt(4 eps' + 9) - 3) / 2 (so (2+eps)(1+eps) = 2 + eps'),       */
+/*    delta = 2 / eps, in double; thresholds thr[b] = (1+eps)^b by repeated  */
+/*    multiplication from thr[0] = 1; bucket(C) = the smallest b with        */
+/*    thr[b] >= C, i.e. ceil(log_{1+eps} C) decided by comparisons.          */
+/*  - a vertex's estimate is thr[its bucket when peeled] (the worked         */
+/*    example's values); isolated vertices get 0 and are never peeled.      */
+/*  - the outer loop sets t to the lowest non-empty bucket; up to            */
+/*    J = ceil(log_{1+delta} n) inner iterations each peel the whole lowest  */
+/*    bucket, then update every surviving neighbour:                         */
+/*    C = max(C - r, ceil((1+eps)^(t-1))), bucket = max(bucket(C), t); the   */
+/*    next inner iteration runs while thr[next lowest bucket] <=             */
+/*    (2+eps) thr[t].                                                        */
+/* ------------------------------------------------------------------------- */
+#define ORC_MAX_BUCKETS 4096
+
+/* The threshold table and the loop constants; 0 on success. */
+static int static_params(int32_t n, double eps_prime, double *thr, int32_t *nb, int32_t *J, double *eps_out) {
+    if (!(eps_prime > 0.0) || n < 1) return -1;
+    double eps = (sqrt(4.0 * eps_prime + 9.0) - 3.0) / 2.0;
+    if (!(eps > 0.0)) return -1;
+    double delta = 2.0 / eps;
+    /* J = ceil(log_{1+delta} n): the smallest J >= 1 with (1+delta)^J >= n */
+    int32_t j = 1;
+    double p = 1.0 + delta;
+    while (p < (double)n && j < 100000) { p *= 1.0 + delta; ++j; }
+    /* thresholds up to the first one >= n (no degree exceeds n - 1) */
+    int32_t b = 0;
+    thr[0] = 1.0;
+    while (thr[b] < (double)n) {
+        if (b + 1 >= ORC_MAX_BUCKETS) return -1;
+        thr[b + 1] = thr[b] * (1.0 + eps);
+        ++b;
+    }
+    *nb = b + 1;
+    *J = j;
+    *eps_out = eps;
+    return 0;
+}
+
+static int32_t bucket_of(const double *thr, int32_t nb, int32_t c) {
+    int32_t b = 0;
+    while (b < nb - 1 && thr[b] < (double)c) ++b;
+    return b;
+}
+
+/*
+ * est[v] for the current graph of h; stats[0] = outer iterations, stats[1] = inner
+ * iterations (peeled buckets), stats[2] = neighbour visits (may be NULL).
+ */
+int orc_static_coreness(const orc_plds *h, double eps_prime, double *est, int64_t *stats) {
+    const int32_t n = h->n;
+    static double thr[ORC_MAX_BUCKETS];
+    int32_t nb = 0, J = 0;
+    double eps = 0.0;
+    if (static_params(n, eps_prime, thr, &nb, &J, &eps)) return ORC_EINVAL;
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *bk = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *r = (int32_t *)calloc(n, sizeof(int32_t));
+    uint8_t *alive = (uint8_t *)calloc(n, 1), *inI = (uint8_t *)calloc(n, 1);
+    if (!C || !bk || !r || !alive || !inI) {
+        free(C); free(bk); free(r); free(alive); free(inI);
+        return ORC_ENOMEM;
+    }
+    int64_t left = 0, outer = 0, inner = 0, visits = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        est[v] = 0.0;
+        C[v] = h->deg[v];
+        if (C[v] > 0) {
+            alive[v] = 1;
+            bk[v] = bucket_of(thr, nb, C[v]);
+            ++left;
+        }
+    }
+    while (left > 0) {
+        int32_t bkt = nb;
+        for (int32_t v = 0; v < n; ++v)
+            if (alive[v] && bk[v] < bkt) bkt = bk[v];
+        const int32_t t = bkt;
+        ++outer;
+        /* ceil((1+eps)^(t-1)): 1 for t = 0 */
+        const int32_t floor_c = t == 0 ? 1 : (int32_t)ceil(thr[t - 1]);
+        for (int32_t j = 0; j < J; ++j) {
+            ++inner;
+            /* I: the whole bucket bkt */
+            for (int32_t v = 0; v < n; ++v)
+                if (alive[v] && bk[v] == bkt) {
+                    inI[v] = 1;
+                    alive[v] = 0;
+                    est[v] = thr[bkt];
+                    --left;
+                }
+            /* R: r_v = neighbours of v in I, for surviving v */
+            for (int32_t u = 0; u < n; ++u) {
+                if (!inI[u]) continue;
+                for (int32_t k = 0; k < h->deg[u]; ++k) {
+                    int32_t v = h->nbr[u][k];
+                    ++visits;
+                    if (alive[v]) r[v]++;
+                }
+            }
+            for (int32_t v = 0; v < n; ++v) {
+                inI[v] = 0;
+                if (!r[v]) continue;
+                int32_t c = C[v] - r[v];
+                C[v] = c > floor_c ? c : floor_c;
+                int32_t nbk = bucket_of(thr, nb, C[v]);
+                bk[v] = nbk > t ? nbk : t;
+                r[v] = 0;
+            }
+            if (left == 0) break;
+            int32_t next = nb;
+            for (int32_t v = 0; v < n; ++v)
+                if (alive[v] && bk[v] < next) next = bk[v];
+            if (thr[next] <= (2.0 + eps) * thr[t]) bkt = next;
+            else break;
+        }
+    }
+    if (stats) { stats[0] = outer; stats[1] = inner; stats[2] = visits; }
+    free(C); free(bk); free(r); free(alive); free(inI);
+    return ORC_OK;
+}
+
+/* The threshold table (for the tests): up to cap entries; returns the count. */
+int32_t orc_static_thresholds(int32_t n, double eps_prime, double *thr_out, int32_t cap, int32_t *J) {
+    static double thr[ORC_MAX_BUCKETS];
+    int32_t nb = 0;
+    double eps = 0.0;
+    if (static_params(n, eps_prime, thr, &nb, J, &eps)) return ORC_EINVAL;
+    for (int32_t i = 0; i < nb && i < cap; ++i) thr_out[i] = thr[i];
+    return nb;
 }

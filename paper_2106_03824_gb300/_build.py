@@ -26,7 +26,9 @@ def _nvcc() -> str:
 
 
 def _flags(src: str):
-    f = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(CSRC), "-I", str(INC)]
+    # host code: no fused multiply-add contraction (threshold tables in double must round
+    # the same way on every host)
+    f = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", str(CSRC), "-I", str(INC)]
     if src.endswith(".cu"):
         f += ARCH + ["-lineinfo", "-Xptxas", "-dlcm=cg", "--expt-relaxed-constexpr"]
         if os.environ.get("PLDS_PTXAS_VERBOSE"):

@@ -150,6 +150,7 @@ struct plds {
     int64_t pool_live = 0;   // slots in use after the last compaction
     // orientation tracking: levels before the last batch call, its kind, validity
     DevBuf old_level, oscratch, okeys;
+    DevBuf sk_scratch, sk_tables, sk_ctl;  // static approximate k-core
     int32_t orient_op = -1;
     bool orient_ok = false;
     int64_t pool_limit = 0;  // bytes a grown pool may take (0: free HBM only)
@@ -228,7 +229,7 @@ static void free_all(plds *h) {
                       &h->pool_top, &h->ctl, &h->acc,   &h->M[0],  &h->M[1],  &h->TL[0], &h->TL[1], &h->TL[2],
                       &h->P[0],  &h->P[1],  &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0], &h->CL[1],
                       &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace,
-                      &h->old_level, &h->oscratch, &h->okeys};
+                      &h->old_level, &h->oscratch, &h->okeys, &h->sk_scratch, &h->sk_tables, &h->sk_ctl};
     for (DevBuf *b : bufs) dev_free(h, *b);
 }
 
@@ -905,6 +906,236 @@ int plds_oriented_updates(plds_t *h, int32_t *out, int64_t cap, int64_t *count) 
     k_oriented_updates<<<orient_grid(h), 256, 0, h->stream>>>(P<unsigned long long>(h->vkeys), m, lv, lst);
     h->launches++;
     return set_status(pairs_out(h, out, cap, lst, m));
+}
+
+// ---------------------------------------------------------------------------
+// Static (2+eps')-approximate k-core (Section "Static (2+eps)-Approximate k-Core",
+// Algorithm 6) on the handle's current graph, without touching its levels: one
+// cooperative kernel, three grid-barrier phases per peeling iteration -- select
+// (peel the lowest bucket, compact the survivors), count (each peeled vertex's
+// surviving neighbours: r_v by atomics), update (over all survivors: those with
+// r_v > 0 get C = max(C - r, ceil((1+eps)^(t-1))) and bucket = max(bucket(C), t);
+// every survivor's bucket enters the minimum that picks the next bucket).  Buckets are decided by comparing integers with the
+// host-built table thr[b] = (1+eps)^b, so the estimates thr[bucket when peeled]
+// are exact copies of the table's doubles.
+// ---------------------------------------------------------------------------
+namespace {
+struct StaticCtl {
+    unsigned long long bar_arrivals;  // grid barrier (same layout as Ctl's first word)
+    int32_t err;
+    int32_t acnt[2];    // alive lists
+    int32_t icnt;       // peeled in this iteration
+    int32_t minb[3];    // lowest bucket among survivors (per iteration mod 3)
+    unsigned long long outer, inner, visits;
+};
+struct StaticArgs {
+    int32_t n, nb, J;
+    const int32_t *deg, *cap;
+    const int64_t *off;
+    const int32_t *slots;
+    const double *thr, *lim;
+    const int32_t *floor_c;
+    int32_t *C, *bk, *r, *A0, *A1, *I;
+    double *est;
+    StaticCtl *sc;
+    int64_t wait_limit_ns;
+};
+}  // namespace
+
+__device__ __forceinline__ int32_t sk_bucket(const double *thr, int32_t nb, int32_t c) {
+    int32_t lo = 0, hi = nb - 1;  // the smallest b with thr[b] >= c (thr is increasing)
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (thr[mid] >= (double)c) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(512) k_static_core(const StaticArgs a) {
+    GridTeam T{reinterpret_cast<Ctl *>(a.sc), a.wait_limit_ns, 32};
+    StaticCtl *sc = a.sc;
+    const int lane = threadIdx.x & 31;
+    unsigned long long visits = 0;
+    // init: C = deg, bucket of C, alive list; isolated vertices get 0
+    for (int64_t v = T.tid(); v < a.n; v += T.nthreads()) {
+        const int32_t d = a.deg[v];
+        a.C[v] = d;
+        a.r[v] = 0;
+        a.est[v] = 0.0;
+        int32_t b = -1;
+        if (d > 0) {
+            b = sk_bucket(a.thr, a.nb, d);
+            a.A0[atomicAdd(&sc->acnt[0], 1)] = (int32_t)v;
+            atomicMin(&sc->minb[0], b);
+        }
+        a.bk[v] = b;
+    }
+    if (!T.sync()) return;
+    int32_t t = ld_volatile(&sc->minb[0]), bkt = t, j = 0;
+    for (int it = 1;; ++it) {
+        if (ld_volatile(&sc->acnt[(it - 1) & 1]) == 0) break;
+        const int cur = (it - 1) & 1, nxt = it & 1, w = it % 3;
+        const int32_t ac = ld_volatile(&sc->acnt[cur]);
+        const int32_t *A = cur ? a.A1 : a.A0;
+        int32_t *An = nxt ? a.A1 : a.A0;
+        if (T.leader()) {
+            sc->minb[(it + 1) % 3] = 0x7fffffff;  // written in iteration it + 1, last read two barriers ago
+            sc->inner += 1;
+            if (j == 0) sc->outer += 1;
+        }
+        // select: peel bucket bkt, keep the rest
+        for (int64_t i0 = (int64_t)T.wid() * 32; i0 < ac; i0 += (int64_t)T.nwarps() * 32) {
+            const int64_t i = i0 + lane;
+            int32_t v = 0, b = -1;
+            if (i < ac) {
+                v = A[i];
+                b = a.bk[v];
+            }
+            const bool peel = i < ac && b == bkt, keep = i < ac && b != bkt;
+            if (peel) {
+                a.bk[v] = -1;
+                a.est[v] = a.thr[bkt];
+            }
+            const int pi = warp_append(&sc->icnt, peel);
+            if (peel) a.I[pi] = v;
+            const int pk = warp_append(&sc->acnt[nxt], keep);
+            if (keep) An[pk] = v;
+        }
+        if (!T.sync()) return;
+        // count: surviving neighbours of the peeled vertices
+        const int32_t ic = ld_volatile(&sc->icnt);
+        if (T.leader()) sc->acnt[cur] = 0;  // read by every thread before the barrier
+        for (int64_t i = T.wid(); i < ic; i += T.nwarps()) {
+            const int32_t u = a.I[i];
+            const int4 *tb = reinterpret_cast<const int4 *>(a.slots + a.off[u]);
+            const int32_t ng = a.cap[u] >> 2;
+            for (int32_t g0 = 0; g0 < ng; g0 += 32) {
+                const int32_t gi = g0 + lane;
+                const int4 q = gi < ng ? tb[gi] : make_int4(-1, -1, -1, -1);
+                const int32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t x = w4[k];
+                    if (x >= 0 && x < a.n) {
+                        ++visits;
+                        if (a.bk[x] >= 0) atomicAdd(&a.r[x], 1);
+                    }
+                }
+            }
+        }
+        if (!T.sync()) return;
+        // update: the survivors that lost neighbours; the lowest bucket of all survivors
+        const int32_t sn = ld_volatile(&sc->acnt[nxt]);
+        if (T.leader()) sc->icnt = 0;
+        int32_t mu = 0x7fffffff;
+        for (int64_t i = T.tid(); i < sn; i += T.nthreads()) {
+            const int32_t x = An[i];
+            const int32_t rx = a.r[x];
+            int32_t b = a.bk[x];
+            if (rx > 0) {
+                const int32_t c = max(a.C[x] - rx, a.floor_c[t]);
+                a.C[x] = c;
+                a.r[x] = 0;
+                b = max(sk_bucket(a.thr, a.nb, c), t);
+                a.bk[x] = b;
+            }
+            mu = min(mu, b);
+        }
+        mu = (int32_t)__reduce_min_sync(kFull, (unsigned)mu);
+        if (lane == 0 && mu != 0x7fffffff) atomicMin(&sc->minb[w], mu);
+        if (!T.sync()) return;
+        // next: another bucket at the same threshold t while it is within (2+eps) thr[t]
+        if (ld_volatile(&sc->acnt[nxt]) == 0) break;
+        const int32_t next = ld_volatile(&sc->minb[w]);
+        if (next < 0 || next >= a.nb) {
+            if (T.leader()) {
+                atomicOr(&sc->err, kErrInternal);
+            }
+            return;
+        }
+        if (j + 1 < a.J && a.thr[next] <= a.lim[t]) {
+            bkt = next;
+            ++j;
+        } else {
+            t = next;
+            bkt = next;
+            j = 0;
+        }
+    }
+    visits = warp_sum64(visits);
+    if (lane == 0 && visits) atomicAdd(&sc->visits, visits);
+}
+
+int plds_static_coreness(plds_t *h, double eps_prime, double *out, int64_t *stats) {
+    if (!h || !out) return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    StaticTables tb;
+    if (build_static_tables(h->n, eps_prime, &tb) != 0) return set_status(PLDS_EINVAL);
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->n, nb = tb.thr.size();
+    const bool dout = is_device_ptr(out);
+    if (!dev_get(h, h->sk_scratch, 4 * N * 6 + (dout ? 0 : 8 * N) + 64) ||
+        !dev_get(h, h->sk_tables, 16 * nb + 4 * nb + 64) || !dev_get(h, h->sk_ctl, sizeof(StaticCtl)))
+        return set_status(PLDS_ENOMEM);
+    std::vector<unsigned char> host(16 * nb + 4 * nb);
+    std::memcpy(host.data(), tb.thr.data(), 8 * nb);
+    std::memcpy(host.data() + 8 * nb, tb.lim.data(), 8 * nb);
+    std::memcpy(host.data() + 16 * nb, tb.floor_c.data(), 4 * nb);
+    cudaMemcpyAsync(h->sk_tables.p, host.data(), host.size(), cudaMemcpyHostToDevice, h->stream);
+    StaticCtl c0{};
+    c0.minb[0] = c0.minb[1] = c0.minb[2] = 0x7fffffff;
+    cudaMemcpyAsync(h->sk_ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice, h->stream);
+    int32_t *w = P<int32_t>(h->sk_scratch);
+    StaticArgs a{};
+    a.n = h->n;
+    a.nb = (int32_t)nb;
+    a.J = tb.J;
+    a.deg = P<int32_t>(h->deg);
+    a.cap = P<int32_t>(h->cap);
+    a.off = P<int64_t>(h->off);
+    a.slots = P<int32_t>(h->pool);
+    a.thr = P<double>(h->sk_tables);
+    a.lim = a.thr + nb;
+    a.floor_c = reinterpret_cast<const int32_t *>(a.thr + 2 * nb);
+    a.C = w;
+    a.bk = w + N;
+    a.r = w + 2 * N;
+    a.A0 = w + 3 * N;
+    a.A1 = w + 4 * N;
+    a.I = w + 5 * N;
+    a.est = dout ? out : reinterpret_cast<double *>(P<unsigned char>(h->sk_scratch) + ((4 * N * 6 + 15) & ~(size_t)15));
+    a.sc = P<StaticCtl>(h->sk_ctl);
+    a.wait_limit_ns = h->wait_limit_ns;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_static_core, 512, 0);
+    if (occ < 1) return set_status(PLDS_EDEVICE);
+    void *args[] = {(void *)&a};
+    if (cudaLaunchCooperativeKernel((const void *)k_static_core, dim3(h->num_sms), dim3(512), args, 0, h->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return set_status(PLDS_EDEVICE);
+    }
+    h->launches++;
+    StaticCtl c{};
+    cudaMemcpyAsync(&c, h->sk_ctl.p, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+    if (!dout) cudaMemcpyAsync(out, a.est, 8 * N, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->poisoned = true;
+        return set_status(PLDS_EDEVICE);
+    }
+    if (c.err & kErrTimeout) {
+        h->poisoned = true;
+        return set_status(PLDS_ETIMEOUT);
+    }
+    if (c.err) return set_status(PLDS_EINTERNAL);
+    if (stats) {
+        stats[0] = (int64_t)c.outer;
+        stats[1] = (int64_t)c.inner;
+        stats[2] = (int64_t)c.visits;
+    }
+    return set_status(PLDS_OK);
 }
 
 int plds_levels(plds_t *h, int32_t *out) {

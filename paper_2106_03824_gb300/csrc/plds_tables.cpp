@@ -169,4 +169,28 @@ int32_t opt_levels_per_group(int64_t m, double delta) {
     return -1;
 }
 
+int build_static_tables(int32_t n, double eps_prime, StaticTables *out) {
+    if (n < 1 || !(eps_prime > 0) || eps_prime > 1e9) return -1;
+    const double eps = (std::sqrt(4.0 * eps_prime + 9.0) - 3.0) / 2.0;
+    if (!(eps > 0)) return -1;
+    const double delta = 2.0 / eps;
+    int32_t J = 1;
+    for (double p = 1.0 + delta; p < (double)n && J < 100000; p *= 1.0 + delta) ++J;
+    out->thr.assign(1, 1.0);
+    while (out->thr.back() < (double)n) {
+        if (out->thr.size() >= 4096) return -1;
+        out->thr.push_back(out->thr.back() * (1.0 + eps));
+    }
+    const size_t nb = out->thr.size();
+    out->lim.resize(nb);
+    out->floor_c.resize(nb);
+    for (size_t t = 0; t < nb; ++t) {
+        out->lim[t] = (2.0 + eps) * out->thr[t];
+        out->floor_c[t] = t == 0 ? 1 : (int32_t)std::ceil(out->thr[t - 1]);
+    }
+    out->J = J;
+    out->eps = eps;
+    return 0;
+}
+
 }  // namespace pl

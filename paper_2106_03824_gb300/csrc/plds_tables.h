@@ -26,4 +26,16 @@ int build_tables(int32_t n, double delta, double lambda, int32_t levels_per_grou
 // (m outside [0, 2^32), delta not positive, or powers beyond 20000 bits).
 int32_t opt_levels_per_group(int64_t m, double delta);
 
+// Constants of the static approximate k-core (Algorithm 6) for n vertices:
+// eps = (sqrt(4 eps' + 9) - 3) / 2, delta = 2 / eps; thr[b] = (1+eps)^b by repeated
+// multiplication up to the first value >= n; floor_c[t] = ceil((1+eps)^(t-1)) (1 for
+// t = 0); lim[t] = (2+eps) thr[t]; J = ceil(log_{1+delta} n).  -1 on invalid input.
+struct StaticTables {
+    std::vector<double> thr, lim;
+    std::vector<int32_t> floor_c;
+    int32_t J = 0;
+    double eps = 0;
+};
+int build_static_tables(int32_t n, double eps_prime, StaticTables *out);
+
 }  // namespace pl

@@ -126,6 +126,7 @@ def load():
     L.plds_out_degrees.argtypes = [vp, vp]
     L.plds_flips.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
     L.plds_oriented_updates.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
+    L.plds_static_coreness.argtypes = [vp, dbl, vp, vp]
     L.plds_opt_levels_per_group.argtypes = [i64, dbl]
     L.plds_opt_levels_per_group.restype = i32
     L.plds_last_status.argtypes = []
@@ -278,6 +279,15 @@ class PLDS:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(load().plds_set_tuning(self._h, ctypes.byref(t)), "plds_set_tuning")
+
+    def static_coreness(self, eps_prime: float = 1.0, out=None):
+        """Static (2+eps')-approximate k-core of the current graph (Algorithm 6):
+        (estimates, {outer, inner, visits})."""
+        out = np.zeros(self.n, np.float64) if out is None else out
+        st = np.zeros(3, np.int64)
+        self._check(load().plds_static_coreness(self._h, float(eps_prime), _ptr(out), _ptr(st)),
+                    "plds_static_coreness")
+        return out, dict(outer=int(st[0]), inner=int(st[1]), visits=int(st[2]))
 
     # orientation (Algorithm 5)
     def orient(self, edges) -> np.ndarray:

@@ -46,6 +46,10 @@ MUTANTS = {
     # flips of the last batch compared against the levels after it on both sides
     "flips_no_snapshot": ("int before = goes_from(h->old_level, u, v), after = goes_from(h->level, u, v);",
                           "int before = goes_from(h->level, u, v), after = goes_from(h->level, u, v);"),
+    # static k-core: estimate from the previous threshold (the prose's (1+eps)^(k-1))
+    "static_estimate": ("est[v] = thr[bkt];", "est[v] = bkt > 0 ? thr[bkt - 1] : 0.5;"),
+    # static k-core: the next bucket taken at the same threshold without the (2+eps) test
+    "static_no_threshold_test": ("if (thr[next] <= (2.0 + eps) * thr[t]) bkt = next;", "if (1) bkt = next;"),
     # levels per group 4t replaced by t
     "group_size": ("T->Lg = lg_override > 0 ? lg_override : 4 * (t > 1 ? t : 1);",
                    "T->Lg = lg_override > 0 ? lg_override : (t > 1 ? t : 1);"),

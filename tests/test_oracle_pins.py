@@ -492,3 +492,80 @@ def test_heuristic_coefficient_tables():
     for b in W.batches(W.shuffled(e, 2), 3000):
         assert h.delete(b) == 0
         assert h.check() == 0
+
+
+# ----------------------------------------------------------------------------
+# Static (2+eps')-approximate k-core (Section "Static (2+eps)-Approximate k-Core",
+# Algorithm 6)
+# ----------------------------------------------------------------------------
+
+def _static_graph(n, edges):
+    h = O.OraclePLDS(n, 1.0, 3.0, levels_per_group=3)
+    h.add_edges_raw(edges)
+    return h
+
+
+def test_static_worked_example():
+    """The paper's example with eps = 1 (eps' = 4): v, w, a, b of degree 2 go to
+    bucket ceil(log2 2) = 1 and get 2; u, x, y, z (a K4, one extra neighbour each)
+    keep degree >= 3 after the first peel, stay in bucket 2 and get 4."""
+    u, x, y, z, v, w, a, b = range(8)
+    E = [(u, x), (u, y), (u, z), (x, y), (x, z), (y, z), (v, u), (v, w), (w, x), (a, y), (a, b), (b, z)]
+    est, st = _static_graph(8, E).static_coreness(4.0)
+    assert list(est) == [4, 4, 4, 4, 2, 2, 2, 2]
+    thr, J = O.static_thresholds(8, 4.0)
+    assert list(thr) == [1, 2, 4, 8]          # eps = (sqrt(25) - 3) / 2 = 1 exactly
+    assert J == 2                             # delta = 2: ceil(log_3 8) = 2
+
+
+def test_static_closed_forms():
+    # a clique on k+1 vertices: all peeled together, estimate = (1+eps)^ceil(log_{1+eps} k)
+    k = 9
+    E = [(i, j) for i in range(k + 1) for j in range(i + 1, k + 1)]
+    est, _ = _static_graph(k + 1, E).static_coreness(4.0)
+    assert np.all(est == 16.0)               # ceil(log2 9) = 4
+    # a star: leaves first (bucket 0), the centre drops to the clamp 1 and follows: all 1
+    E = [(0, i) for i in range(1, 40)]
+    est, st = _static_graph(40, E).static_coreness(1.0)
+    assert np.all(est == 1.0) and st["outer"] == 1
+    # isolated vertices: 0; a path: all 1
+    est, _ = _static_graph(6, [(0, 1), (1, 2), (2, 3)]).static_coreness(1.0)
+    assert list(est) == [1, 1, 1, 1, 0, 0]
+
+
+def test_static_within_bound_of_exact():
+    """Estimates are within 2 + eps' of the exact coreness both ways (and 0 exactly
+    on isolated vertices), on power-law graphs and on all graphs of brute-force size."""
+    for ep in (0.5, 1.0, 2.0, 4.0):
+        for seed in range(4):
+            for n, m, gam in ((1500, 12000, 2.2), (300, 6000, 2.1)):
+                e = W.chung_lu(n, m, gam, seed=seed)
+                est, _ = _static_graph(n, e).static_coreness(ep)
+                core = O.exact_coreness(n, e).astype(np.float64)
+                nz = core > 0
+                assert np.array_equal(est == 0, ~nz)
+                assert np.all(est[nz] <= (2 + ep) * core[nz]) and np.all(core[nz] <= (2 + ep) * est[nz])
+    rng = np.random.default_rng(9)
+    for trial in range(40):
+        n = int(rng.integers(2, 11))
+        allp = _ref.all_pairs(n)
+        pick = [allp[i] for i in rng.choice(len(allp), size=int(rng.integers(1, len(allp) + 1)), replace=False)]
+        core = np.asarray(_ref.brute_coreness(n, pick), np.float64)
+        est, _ = _static_graph(n, pick).static_coreness(1.0)
+        nz = core > 0
+        assert np.array_equal(est == 0, ~nz)
+        assert np.all(est[nz] <= 3 * core[nz]) and np.all(core[nz] <= 3 * est[nz])
+
+
+def test_static_threshold_test_traced_example():
+    """A traced run (eps' = 4: eps = 1, delta = 2, J = ceil(log_3 8) = 2, thresholds
+    1, 2, 4, 8).  Degrees 1, 1, 4, 5, 5, 5, 4, 3 give buckets 0, 0, 2, 3, 3, 3, 2, 2.
+    t = 0 peels {0, 1} (estimate 1); 4 and 5 drop to degree 4, bucket 2.  The next
+    bucket fails the test 4 <= (2+1)*1, so t becomes 2: {2, 4, 5, 6, 7} are peeled at
+    4, and 3 (degree 0 left, floored at the bucket t = 2) follows at 4.  Peeling
+    bucket 2 still at t = 0 would have let 3 fall to bucket 0 (estimate 1)."""
+    E = [(0, 5), (1, 4), (2, 3), (2, 4), (2, 6), (2, 7), (3, 4), (3, 5), (3, 6), (3, 7), (4, 5), (4, 6),
+         (5, 6), (5, 7)]
+    est, st = _static_graph(8, E).static_coreness(4.0)
+    assert list(est) == [1, 1, 4, 4, 4, 4, 4, 4]
+    assert st["outer"] == 2 and st["inner"] == 3
