@@ -43,7 +43,7 @@ UNIT = "updates/s"
 # dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": "e3bf78f05dd9ed62", "dram_per_algo_byte": 0.10744, "capture": "profiles/k_batch_grid_traffic_rmat20_B1e6.md"}
+NCU_TRAFFIC = {"kernel_sha": "63d114d01012945d", "dram_per_algo_byte": 0.1295, "capture": "profiles/k_batch_grid_traffic_rmat20_B1e6.md"}
 
 
 def kernel_sha() -> str:
@@ -154,6 +154,18 @@ def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3, levels_per_grou
         tag = "1e6" if B == 1_000_000 else "1e5"
         g = P.PLDS(n, levels_per_group=levels_per_group)
         out[f"ins_{tag}"] = timed(g, [(g.insert, ins_d[s:s + B]) for s in range(0, ins_d.shape[0], B)])
+        if B == sizes[0] and levels_per_group == 0:
+            # the static approximate k-core (Algorithm 6) of the loaded graph
+            d = torch.empty(n, dtype=torch.float64, device="cuda")
+            g.static_coreness(1.0, out=d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = g.static_coreness(1.0, out=d)
+            e1.record()
+            torch.cuda.synchronize()
+            out["static_kcore"] = {"eps_prime": 1.0, "ms": e0.elapsed_time(e1), **st,
+                                   "edges_per_s": int(e.shape[0]) / (e0.elapsed_time(e1) / 1e3)}
         out[f"del_{tag}"] = timed(g, [(g.delete, del_d[s:s + B]) for s in range(0, del_d.shape[0], B)])
         g.close()
     pre, mixes = W.mix_stream(e, 1_000_000, mix_batches, load=0.9, seed=seed)
