@@ -933,9 +933,10 @@ __device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t
 // A mover of level l whose whole table has been scanned (total = its neighbours
 // left on l): new up* = old up (its neighbours on l or above), new up = old up -
 // total, level l + 1; returns true if it violates Invariant 1 on l + 1 as well.
-__device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, int32_t total, int32_t l,
-                                                 int32_t fcur, int32_t fnext, int32_t cut_next) {
-    const int32_t old_up = g.up[v];
+// old_up: the mover's up-degree, read at any time during the round (only this
+// function writes it while the round runs).
+__device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, int32_t old_up, int32_t total,
+                                                 int32_t l, int32_t fcur, int32_t fnext, int32_t cut_next) {
     const int32_t nu = old_up - total;
     g.upstar[v] = old_up;
     g.up[v] = nu;
@@ -995,12 +996,14 @@ __device__ __forceinline__ void marks_add(const GraphCtx &g, const RoundStage &s
     mc += tot;
 }
 
-// Test the initial candidates S[s_lo, s_hi) on level L against Invariant 1.
+// Test the initial candidates S[s_lo, s_hi) on level L against Invariant 1 (warp
+// ranks rotated by rot, so that a small test runs on other warps than a scan).
 template <class Team>
 __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &st, int32_t s_lo, int32_t s_hi,
-                                 int32_t L, int32_t cut, int32_t *wsm) {
+                                 int32_t L, int32_t cut, int32_t *wsm, int rot) {
     const int32_t fl = level_flag(L);
-    for (int i0 = s_lo + T.wid() * 32; i0 < s_hi; i0 += T.nwarps() * 32) {
+    const int rank = (T.wid() + rot) % T.nwarps();
+    for (int i0 = s_lo + rank * 32; i0 < s_hi; i0 += T.nwarps() * 32) {
         const int i = i0 + lane_id();
         bool mk = false;
         int32_t v = 0;
@@ -1046,7 +1049,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
         st.cl.gcap = g.clcap;
         if (!scan) {
             const int32_t s_lo = l == 0 ? 0 : g.bins[l - 1], s_hi = g.bins[l];
-            ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm);
+            ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm, 0);
         } else {
             m = g.ctl->imcnt[cur];
             tlc = g.ctl->itl[cur];
@@ -1058,13 +1061,14 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             const int32_t fcur = level_flag(l), fnext = level_flag(l + 1);
             const int32_t cut_next = sh_upmax[(l + 1) / g.Lg];
             if (spos < nlev && g.levlist[spos] == l + 1)  // initial candidates on l + 1
-                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm);
+                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm, T.nwarps() / 2);
             // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
             for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
                 const int i = i0 + lane;
                 const int4 it = i < tlc ? g.TL[cur][i] : make_int4(0, 0, 0, 0);
                 const bool have = i < tlc && item_ok(g, it, it.y);
                 const int ng = have ? (1 << it.y) >> 2 : 0;
+                const int32_t up_v = have ? g.up[it.x] : 0;  // issued with the slot loads
                 const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
                 int cnt_l = 0;
                 for (int j0 = 0; j0 < maxg; j0 += 4) {
@@ -1085,19 +1089,24 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
                     marks_add(g, st, push, ws, mbuf, mc, wsm);
                 }
-                const bool again = have && ins_finish_mover(g, it.x, cnt_l, l, fcur, fnext, cut_next);
+                const bool again = have && ins_finish_mover(g, it.x, up_v, cnt_l, l, fcur, fnext, cut_next);
                 enqueue_mover(g, st, again, it.x, 0, have ? 1 << it.y : 0, (int64_t)it.z * 4, wsm);
             }
-            // chunk items: four per warp iteration, all loads of a step issued together
-            for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
+            // chunk items: four per warp iteration, all loads of a step issued together;
+            // taken from the last warp down, so that in a small round the warps
+            // scanning thread-mode items and those scanning chunks are different ones
+            const int crank = T.nwarps() - 1 - T.wid();
+            for (int c0 = crank; c0 < clc; c0 += 4 * T.nwarps()) {
                 int4 it[4];
                 bool ok[4], in[4];
                 int32_t ws[16], lv[16];
+                int32_t upl = 0;  // lane u < 4: up-degree of item u's vertex
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int cu = c0 + u * T.nwarps();
                     it[u] = cu < clc ? g.CL[cur][cu] : make_int4(0, 0, 0, 0);
                     ok[u] = cu < clc && item_ok(g, it[u], it[u].y & 31);
+                    if (lane == u && ok[u]) upl = g.up[it[u].x];
                     const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
                     in[u] = ok[u] && j < ((1 << (it[u].y & 31)) >> 2);
                     const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
@@ -1120,6 +1129,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int cnt = warp_sum(cl4[u]);
+                    const int32_t up_u = __shfl_sync(kFull, upl, u);
                     if (lane == 0 && ok[u]) {
                         const int lg = it[u].y & 31;
                         const int nch = max(1, (1 << lg) / kChunk);
@@ -1132,7 +1142,8 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                             total = (int32_t)(uint32_t)(o & 0xffffffffull) + cnt;
                             if (last) g.acc[it[u].x] = 0ull;
                         }
-                        if (last && ins_finish_mover(g, it[u].x, total, l, fcur, fnext, cut_next)) again |= 1u << u;
+                        if (last && ins_finish_mover(g, it[u].x, up_u, total, l, fcur, fnext, cut_next))
+                            again |= 1u << u;
                     }
                 }
                 again = __shfl_sync(kFull, again, 0);
