@@ -43,7 +43,8 @@ UNIT = "updates/s"
 # dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": "63d114d01012945d", "dram_per_algo_byte": 0.1295, "capture": "profiles/k_batch_grid_traffic_rmat20_B1e6.md"}
+NCU_TRAFFIC = {"kernel_sha": None, "dram_per_algo_byte": None,
+               "capture": "ncu DRAM counters of every k_batch_grid launch of the R-MAT 20 Ins and Del protocols"}
 
 
 def kernel_sha() -> str:
@@ -55,13 +56,13 @@ def kernel_sha() -> str:
 
 
 def algo_bytes(s: dict) -> int:
-    """Algorithmic bytes of one batch kernel launch (per-unit figures in the design doc):
-    8 B per submitted edge; 64 B per applied update (2 probes + 2 slot writes of 4 B,
-    6 counter read-modify-writes of 8 B); 4 B per level change + 8 B per neighbour
-    visited by a moving vertex (id + level); 8 B per neighbour visited by a
-    desire-level evaluation."""
-    return (8 * s["submitted"] + 64 * s["valid"] + 4 * s["moves"] + 8 * s["visits"]
-            + 8 * s["dl_visits"])
+    """Algorithmic bytes of one batch kernel launch: 8 B per submitted edge; 64 B per
+    applied update (2 probes + 2 slot writes of 4 B, 6 counter read-modify-writes of
+    8 B); 4 B per level change; 8 B (id + level) per neighbour a move must examine --
+    an insertion move its up-neighbours (up_visits), a deletion move all its
+    neighbours (visits); 8 B per neighbour read by a desire-level evaluation."""
+    moved = s["up_visits"] if s.get("up_visits") else s["visits"]
+    return 8 * s["submitted"] + 64 * s["valid"] + 4 * s["moves"] + 8 * moved + 8 * s["dl_visits"]
 
 
 def measured_peaks():

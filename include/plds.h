@@ -59,10 +59,11 @@ typedef struct plds_stats {
     int64_t valid;       /* updates applied */
     int64_t rounds;      /* levels at which at least one vertex moved */
     int64_t moves;       /* level changes (insert: one level each; delete: one per vertex) */
-    int64_t visits;      /* neighbours scanned by moving vertices (sum of their degrees) */
+    int64_t visits;      /* neighbours of moving vertices: the sum of their degrees over the moves */
     int64_t dl_evals;    /* desire-level computations */
     int64_t dl_visits;   /* neighbours scanned by desire-level computations */
-    int64_t slots_scanned; /* hash slots read by the level rounds (live + empty + tombstone) */
+    int64_t slots_scanned; /* entries read by the level rounds (table slots: live, empty,
+                              tombstone; up-list entries) */
     int64_t pool_slots_used;
     int64_t pool_slots_cap;
     int64_t device_bytes;  /* device memory currently held by the handle */
@@ -72,6 +73,8 @@ typedef struct plds_stats {
     int64_t err_info[3];   /* values seen by that check (diagnostics) */
     int64_t kernel_ns;     /* device time of the last call's batch kernel (CUDA events) */
     int64_t launches;      /* kernels launched by this handle since creation */
+    int64_t up_visits;     /* insertion: up-neighbours of moving vertices, the sum of their
+                              up-degrees over the moves (what a move must examine) */
 } plds_stats_t;
 
 /* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */
@@ -90,6 +93,9 @@ typedef struct plds_tuning {
     int32_t track_orientation; /* 1 = every plds_batch_insert / plds_batch_delete call saves the
                                   levels at its start (4n bytes of device memory and one copy)
                                   so that plds_flips / plds_oriented_updates can report it */
+    int32_t list_cap;         /* insertion: a moving vertex whose table has at least this many
+                                 slots keeps the neighbours still on its level or above in an
+                                 up-list for its next move (0 = default 256; 2^30 = never) */
 } plds_tuning;
 
 /*
@@ -284,13 +290,14 @@ void plds_set_destroy(plds_set_t *s);
 /*
  * Autotuner (the paper has no counterpart: its cutoffs are a multicore design's).
  * The knobs that change only speed -- the thread cutoff (thread_max_cap), the
- * block cutoff (block_cap) and the hash load factor (load_num/load_den) -- are
- * picked by coordinate descent: starting from `start`, each knob in that order
+ * block cutoff (block_cap), the hash load factor (load_num/load_den) and the
+ * up-list cutoff (list_cap) -- are picked by coordinate descent: starting from `start`, each knob in that order
  * takes every value of its candidate list with the others held, and keeps the
  * value of lowest cost (a new value must cost at least 2 % less than the
  * incumbent); passes repeat while one of them improves, within max_trials cost
  * evaluations.  Candidates: thread_max_cap {4, 8, 16, 32, 64}, block_cap {1024,
- * 2048, 4096, 8192, 16384}, load {1/2, 5/8, 3/4, 7/8}.
+ * 2048, 4096, 8192, 16384}, load {1/2, 5/8, 3/4, 7/8}, list_cap {128, 256, 1024,
+ * 2^30}.
  *   plds_tune_search: the search alone, against any cost function (no device use):
  *     cost(t, ctx) returns a cost (seconds) or a negative value to stop the search
  *     with PLDS_EINTERNAL.  *best gets the chosen knobs (the other fields of start

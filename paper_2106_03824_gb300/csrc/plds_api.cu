@@ -156,7 +156,8 @@ struct plds {
     int64_t pool_limit = 0;  // bytes a grown pool may take (0: free HBM only)
     // scratch: n-sized
     DevBuf acc, M[2], TL[3], P[2], R, R2, bins, levlist, CL[3];
-    int64_t clcap = 0;
+    DevBuf lbuf[3], lout, lfill[2];  // insertion up-lists
+    int64_t clcap = 0, lcap = 0;
     // scratch: batch-sized
     DevBuf edges, hset, ukeys, vkeys, touched, S, arena, trace;
     int64_t bcap = 0, hcap = 0, tcap = 0, arena_cap = 0;
@@ -229,16 +230,27 @@ static void free_all(plds *h) {
                       &h->pool_top, &h->ctl, &h->acc,   &h->M[0],  &h->M[1],  &h->TL[0], &h->TL[1], &h->TL[2],
                       &h->P[0],  &h->P[1],  &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0], &h->CL[1],
                       &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace,
-                      &h->old_level, &h->oscratch, &h->okeys, &h->sk_scratch, &h->sk_tables, &h->sk_ctl};
+                      &h->old_level, &h->oscratch, &h->okeys, &h->sk_scratch, &h->sk_tables, &h->sk_ctl,
+                      &h->lbuf[0], &h->lbuf[1], &h->lbuf[2], &h->lout, &h->lfill[0], &h->lfill[1]};
     for (DevBuf *b : bufs) dev_free(h, *b);
 }
 
+// Chunk-item lists (one 128-slot chunk of every table, plus one item per vertex) and
+// the insertion up-list buffers (as many entries as the pool, at most 2^27 each: a
+// mover whose list does not fit is scanned from its table again).
 static bool alloc_chunk_lists(plds *h) {
     int64_t need = h->pool_cap / kChunk + (int64_t)h->n + 1024;
-    if (h->clcap >= need) return true;
-    for (int i = 0; i < 3; ++i)
-        if (!dev_get(h, h->CL[i], sizeof(int4) * (size_t)need)) return false;
-    h->clcap = need;
+    if (h->clcap < need) {
+        for (int i = 0; i < 3; ++i)
+            if (!dev_get(h, h->CL[i], sizeof(int4) * (size_t)need)) return false;
+        h->clcap = need;
+    }
+    const int64_t lneed = (std::min<int64_t>(std::max<int64_t>(h->pool_cap, 4096), (int64_t)1 << 27) + 3) & ~(int64_t)3;
+    if (h->lcap < lneed) {
+        for (int i = 0; i < 3; ++i)
+            if (!dev_get(h, h->lbuf[i], sizeof(int32_t) * (size_t)lneed)) return false;
+        h->lcap = lneed;
+    }
     return true;
 }
 
@@ -359,6 +371,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.load_num = h->tune.load_num > 0 ? h->tune.load_num : 3;
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
     g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 4096;
+    g.list_cap = h->tune.list_cap > 0 ? h->tune.list_cap : 256;
     g.wait_limit_ns = h->wait_limit_ns;
     g.test_delay_us = h->tune.test_delay_us;
     g.barrier_sleep_ns = h->tune.barrier_sleep_ns == 0 ? 32 : (h->tune.barrier_sleep_ns < 0 ? 0 : h->tune.barrier_sleep_ns);
@@ -396,6 +409,11 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
         g.CL[i] = P<int4>(h->CL[i]);
     }
     g.acc = P<unsigned long long>(h->acc);
+    for (int i = 0; i < 3; ++i) g.lbuf[i] = P<int32_t>(h->lbuf[i]);
+    g.lcap = h->lcap;
+    g.lout = P<int32_t>(h->lout);
+    g.lfill[0] = P<int32_t>(h->lfill[0]);
+    g.lfill[1] = P<int32_t>(h->lfill[1]);
     g.R[0] = P<int32_t>(h->R);
     g.R[1] = P<int32_t>(h->R2);
     g.clcap = h->clcap;
@@ -515,6 +533,7 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
     h->last.dl_evals = (int64_t)c.st[kStDlEvals];
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
+    h->last.up_visits = (int64_t)c.st[kStUpVisits];
     h->orient_ok = h->tune.track_orientation != 0;
     return PLDS_OK;
 }
@@ -563,6 +582,7 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
               dev_get(h, h->tomb, 4 * N) && dev_get(h, h->stamp, 4 * N) && dev_get(h, h->dlv, 4 * N) &&
               dev_get(h, h->inc, 4 * N) && dev_get(h, h->pool, 4 * (size_t)h->pool_cap) &&
               dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->acc, 8 * N) &&
+              dev_get(h, h->lout, 4 * N) && dev_get(h, h->lfill[0], 4 * N) && dev_get(h, h->lfill[1], 4 * N) &&
               dev_get(h, h->M[0], 16 * N) && dev_get(h, h->M[1], 16 * N) && dev_get(h, h->TL[0], 16 * N) &&
               dev_get(h, h->TL[1], 16 * N) && dev_get(h, h->TL[2], 16 * N) && dev_get(h, h->P[0], 32 * N) &&
               dev_get(h, h->P[1], 32 * N) && dev_get(h, h->R, 4 * N) && dev_get(h, h->R2, 4 * N) && dev_get(h, h->bins, 4 * (K + 1)) &&
@@ -1198,7 +1218,8 @@ int plds_set_tuning(plds_t *h, const plds_tuning *t) {
         return set_status(PLDS_EINVAL);
     if (t->thread_max_cap < 0 || t->load_num < 0 || t->load_den < 0 || t->blocks_per_sm < 0 ||
         t->test_delay_us < 0 || t->test_delay_us > 10 * 1000 * 1000 || t->barrier_sleep_ns < -1 ||
-        t->barrier_sleep_ns > 100000 || t->block_cap < 0 || (t->block_cap > 0 && t->block_cap < 4))
+        t->barrier_sleep_ns > 100000 || t->block_cap < 0 || (t->block_cap > 0 && t->block_cap < 4) ||
+        t->list_cap < 0)
         return set_status(PLDS_EINVAL);
     if ((t->load_num > 0) != (t->load_den > 0) || (t->load_num > 0 && (t->load_num * 8 > t->load_den * 7)))
         return set_status(PLDS_EINVAL);  // a table must keep an empty slot
@@ -1366,6 +1387,7 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     h->last.dl_evals = (int64_t)c.st[kStDlEvals];
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
+    h->last.up_visits = (int64_t)c.st[kStUpVisits];
     return set_status(PLDS_OK);
 }
 
@@ -1639,6 +1661,7 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
                 h->last.dl_evals += (int64_t)c->st[kStDlEvals];
                 h->last.dl_visits += (int64_t)c->st[kStDlVisits];
                 h->last.slots_scanned += (int64_t)c->st[kStSlotsScanned];
+                h->last.up_visits += (int64_t)c->st[kStUpVisits];
             }
             const int64_t bi = offsets[2 * gi + 1] - offsets[2 * gi], bd = offsets[2 * gi + 2] - offsets[2 * gi + 1];
             h->last.duplicates = (bi > 0 ? bi - (int64_t)ci.st[kStSelfLoops] - (int64_t)ci.ucount : 0) +
@@ -1657,6 +1680,7 @@ extern "C" int plds_set_tune(plds_set_t *s, const plds_tuning *t) {
         x.block_cap = t->block_cap;
         x.load_num = t->load_num;
         x.load_den = t->load_den;
+        x.list_cap = t->list_cap;
         const int rc = plds_set_tuning(h, &x);
         if (rc) return rc;
     }
@@ -1670,10 +1694,11 @@ namespace {
 constexpr int32_t kTuneThread[] = {4, 8, 16, 32, 64};
 constexpr int32_t kTuneBlock[] = {1024, 2048, 4096, 8192, 16384};
 constexpr int32_t kTuneLoad[][2] = {{1, 2}, {5, 8}, {3, 4}, {7, 8}};
+constexpr int32_t kTuneList[] = {128, 256, 1024, 1 << 30};
 
 bool same_knobs(const plds_tuning &a, const plds_tuning &b) {
     return a.thread_max_cap == b.thread_max_cap && a.block_cap == b.block_cap && a.load_num == b.load_num &&
-           a.load_den == b.load_den;
+           a.load_den == b.load_den && a.list_cap == b.list_cap;
 }
 
 struct SetTuneCtx {
@@ -1722,6 +1747,7 @@ extern "C" int plds_tune_search(const plds_tuning *start, plds_tune_cost cost, v
         cur.load_num = 3;
         cur.load_den = 4;
     }
+    if (cur.list_cap <= 0) cur.list_cap = 256;
     std::vector<std::pair<plds_tuning, double>> seen;  // every evaluation, to skip repeats
     int32_t trials = 0;
     // 0: cost in *c; 1: budget spent; -1: the cost function gave up
@@ -1744,17 +1770,19 @@ extern "C" int plds_tune_search(const plds_tuning *start, plds_tune_cost cost, v
     bool improved = true, spent = false;
     while (improved && !spent) {
         improved = false;
-        for (int knob = 0; knob < 3 && !spent; ++knob) {
-            const int nv = knob == 2 ? 4 : 5;
+        for (int knob = 0; knob < 4 && !spent; ++knob) {
+            const int nv = knob >= 2 ? 4 : 5;
             for (int v = 0; v < nv; ++v) {
                 plds_tuning t = cur;
                 if (knob == 0) {
                     t.thread_max_cap = kTuneThread[v];
                 } else if (knob == 1) {
                     t.block_cap = kTuneBlock[v];
-                } else {
+                } else if (knob == 2) {
                     t.load_num = kTuneLoad[v][0];
                     t.load_den = kTuneLoad[v][1];
+                } else {
+                    t.list_cap = kTuneList[v];
                 }
                 if (same_knobs(t, cur)) continue;
                 double c = 0.0;

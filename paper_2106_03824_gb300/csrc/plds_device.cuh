@@ -829,6 +829,67 @@ __device__ __forceinline__ void enqueue_mover(const GraphCtx &g, const RoundStag
     __syncwarp();
 }
 
+// Insertion: queue the scans of the lanes' movers of the next level.  A mover whose
+// table has at most thread_max_cap slots is scanned by one thread; any other is
+// scanned in 128-entry chunks, from its table (ilen < 0) or from its up-list of
+// ilen entries at int4 offset ioff4 of the list buffer the round writes (a mover
+// that keeps climbing), and gets room for rsize entries in list buffer k1 mod 3 for the
+// neighbours that stay relevant after its move (lout = -1 when the buffer is full:
+// the next scan then reads the table again).  Chunk items of a list carry 31 as
+// their table size and the list length as aux.
+__device__ __forceinline__ void enqueue_ins(const GraphCtx &g, const RoundStage &st, bool is_mover, int32_t v,
+                                            int32_t c, int64_t off, int32_t ilen, int32_t ioff4, int32_t rsize,
+                                            int k1, int32_t *wsm) {
+    const int abuf = k1 % 3;  // k1: index of the phase that scans these movers
+
+    const int lane = lane_id();
+    const unsigned mm = __ballot_sync(kFull, is_mover);
+    if (mm == 0) return;
+    if (lane == __ffs(mm) - 1) atomicAdd(st.movers, __popc(mm));
+    const bool list = is_mover && ilen >= 0;
+    const bool small = is_mover && !list && c <= g.thread_max_cap;
+    const int lg = (is_mover && !list) ? __ffs(c) - 1 : 31;
+    const int32_t goff = list ? ioff4 : (int32_t)(off >> 2);
+    stage_push(st.tl, small, make_int4(v, lg, goff, 0));
+    const bool chunked = is_mover && !small;
+    const bool want = chunked && (list || c >= g.list_cap);  // smaller tables: rescanning is cheaper
+    int tot4;
+    const int ex4 = warp_exclusive(want ? (rsize + 3) >> 2 : 0, &tot4);
+    unsigned long long lbase = 0;
+    if (lane == 0 && tot4 > 0) lbase = atomicAdd(&g.ctl->ltop[abuf], (unsigned long long)tot4);
+    lbase = __shfl_sync(kFull, lbase, 0);
+    if (chunked) {
+        const bool fits = want && lbase + (unsigned long long)tot4 <= (unsigned long long)(g.lcap >> 2);
+        g.lout[v] = fits ? (int32_t)(lbase + (unsigned long long)ex4) : -1;
+        g.lfill[k1 & 1][v] = 0;  // the next phase's counters: last used two phases ago
+    }
+    const int nch = chunked ? (list ? max(1, (ilen + kChunk - 1) / kChunk) : (c + kChunk - 1) / kChunk) : 0;
+    int tot;
+    const int ex = warp_exclusive(nch, &tot);
+    if (tot == 0) return;
+    int pos = 0;
+    bool sh = false;
+    if (lane == 0) pos = stage_reserve(st.cl, tot, sh);
+    pos = __shfl_sync(kFull, pos, 0);
+    sh = __shfl_sync(kFull, sh, 0);
+    wsm[lane] = ex;
+    wsm[32 + lane] = v;
+    wsm[64 + lane] = lg;
+    wsm[96 + lane] = goff;
+    wsm[128 + lane] = list ? ilen : 0;
+    __syncwarp();
+    for (int t = lane; t < tot; t += 32) {
+        int lo = 0, hi = 31;  // owner: the last lane whose range starts at or before t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (wsm[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        stage_put(st.cl, sh, pos + t,
+                  make_int4(wsm[32 + lo], ((t - wsm[lo]) << 5) | wsm[64 + lo], wsm[96 + lo], wsm[128 + lo]));
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Step A4: insertion rounds (Algorithm 2).
 // ---------------------------------------------------------------------------
@@ -913,21 +974,25 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int32_t level_flag(int32_t l) { return (l & 1) ? kFlagOdd : kFlagEven; }
 
-// Effects of a mover of level l on its neighbour w (level word raw).  Returns true
-// if w became a mover of level l + 1 here.
-__device__ __forceinline__ bool ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t fcur,
-                                           int32_t fnext, int32_t cut_next, int &cnt_l) {
-    if (!valid_id(g, w)) return false;  // empty slot or tombstone
+// Effects of a mover of level l on its neighbour w (level word raw).  Returns bit 0
+// if w became a mover of level l + 1 here, bit 1 if w stays on level l + 1 or above
+// after the round (an entry of the mover's up-list for its next move).
+__device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t fcur,
+                                          int32_t fnext, int32_t cut_next, int &cnt_l) {
+    if (!valid_id(g, w)) return 0;  // empty slot or tombstone
     const int32_t f = raw & kLevelMask;
-    if ((raw & fcur) && (f == l || f == l + 1)) return false;  // a mover of level l as well
+    if ((raw & fcur) && (f == l || f == l + 1)) return 2;  // a mover of level l as well
     if (f == l) {
         cnt_l++;
-    } else if (f == l + 1) {
-        if (atomicAdd(&g.up[w], 1) == cut_next) return !(atomicOr(&g.level[w], fnext) & fnext);
+        return 0;
+    }
+    if (f < l) return 0;
+    if (f == l + 1) {
+        if (atomicAdd(&g.up[w], 1) == cut_next) return 2 | (!(atomicOr(&g.level[w], fnext) & fnext) ? 1 : 0);
     } else if (f == l + 2) {
         atomicAdd(&g.upstar[w], 1);
     }
-    return false;
+    return 2;
 }
 
 // A mover of level l whose whole table has been scanned (total = its neighbours
@@ -945,16 +1010,18 @@ __device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, i
     return again;
 }
 
-// Queue the table scans of the lanes' newly marked vertices.
+// Queue the table scans of the lanes' newly marked vertices (their first move of
+// the batch: up-list room for all their neighbours).
 __device__ __forceinline__ void enqueue_marked(const GraphCtx &g, const RoundStage &st, bool mk, int32_t w,
-                                               int32_t *wsm) {
-    int32_t c = 0;
+                                               int k1, int32_t *wsm) {
+    int32_t c = 0, d = 0;
     int64_t off = 0;
     if (mk) {
         c = g.cap[w];
         off = g.off[w];
+        d = g.deg[w];
     }
-    enqueue_mover(g, st, mk, w, 0, c, off, wsm);
+    enqueue_ins(g, st, mk, w, c, off, -1, 0, d, k1, wsm);
 }
 
 // Marked neighbours wait in a per-warp buffer (kMarkCap ids in the warp's shared
@@ -963,11 +1030,11 @@ __device__ __forceinline__ void enqueue_marked(const GraphCtx &g, const RoundSta
 constexpr int kMarkCap = 256;
 
 __device__ __forceinline__ void marks_flush(const GraphCtx &g, const RoundStage &st, int32_t *mbuf, int &mc,
-                                            int32_t *wsm) {
+                                            int k1, int32_t *wsm) {
     for (int b = 0; b < mc; b += 32) {
         const int i = b + lane_id();
         const bool mk = i < mc;
-        enqueue_marked(g, st, mk, mk ? mbuf[i] : 0, wsm);
+        enqueue_marked(g, st, mk, mk ? mbuf[i] : 0, k1, wsm);
     }
     __syncwarp();
     mc = 0;
@@ -975,16 +1042,16 @@ __device__ __forceinline__ void marks_flush(const GraphCtx &g, const RoundStage 
 
 // Append the lanes' marked neighbours (bits of push over ws); mc is warp-uniform.
 __device__ __forceinline__ void marks_add(const GraphCtx &g, const RoundStage &st, unsigned push,
-                                          const int32_t (&ws)[16], int32_t *mbuf, int &mc, int32_t *wsm) {
+                                          const int32_t (&ws)[16], int32_t *mbuf, int &mc, int k1, int32_t *wsm) {
     int tot;
     const int ex = warp_exclusive(__popc(push), &tot);
     if (tot == 0) return;
-    if (mc + tot > kMarkCap) marks_flush(g, st, mbuf, mc, wsm);
+    if (mc + tot > kMarkCap) marks_flush(g, st, mbuf, mc, k1, wsm);
     if (tot > kMarkCap) {  // more than the buffer holds: queue them one slot position at a time
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const bool mk = (push >> q) & 1u;
-            if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], wsm);
+            if (__any_sync(kFull, mk)) enqueue_marked(g, st, mk, ws[q], k1, wsm);
         }
         return;
     }
@@ -1000,7 +1067,7 @@ __device__ __forceinline__ void marks_add(const GraphCtx &g, const RoundStage &s
 // ranks rotated by rot, so that a small test runs on other warps than a scan).
 template <class Team>
 __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &st, int32_t s_lo, int32_t s_hi,
-                                 int32_t L, int32_t cut, int32_t *wsm, int rot) {
+                                 int32_t L, int32_t cut, int32_t *wsm, int rot, int k1) {
     const int32_t fl = level_flag(L);
     const int rank = (T.wid() + rot) % T.nwarps();
     for (int i0 = s_lo + rank * 32; i0 < s_hi; i0 += T.nwarps() * 32) {
@@ -1013,13 +1080,13 @@ __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &s
             if ((raw & kLevelMask) != L) report(g, kErrInternal, 6, v, raw, L);
             else if (g.up[v] > cut) mk = !(atomicOr(&g.level[v], fl) & fl);
         }
-        enqueue_marked(g, st, mk, v, wsm);
+        enqueue_marked(g, st, mk, v, k1, wsm);
     }
 }
 
 template <class Team>
 __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *wsm, RoundStage st) {
-    unsigned long long visits = 0, scanned = 0;
+    unsigned long long visits = 0, scanned = 0, upv = 0;
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     const int32_t nlev = g.ctl->nlev;
@@ -1034,12 +1101,18 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             return false;
         }
         const int cur = k % 3, nxt = (k + 1) % 3, old = (k + 2) % 3;
+        // up-lists: read from buffer old (written in phase k - 1), written to buffer
+        // cur (room handed out in phase k - 1), room handed out now from buffer nxt
+        const int32_t *lin = g.lbuf[old];
+        int32_t *lwr = g.lbuf[cur];
+        int32_t *fill_cur = g.lfill[k & 1];  // reset when this phase's movers were queued
         const uint64_t t_phase = (g.trace && T.leader()) ? global_ns() : 0;
         int32_t tlc = 0, clc = 0, m = 0;
         if (T.leader()) {  // the lists of phase k - 1 are done with; phase k + 1 fills them next
             g.ctl->itl[old] = 0;
             g.ctl->icl[old] = 0;
             g.ctl->imcnt[old] = 0;
+            g.ctl->ltop[old] = 0;  // allocated from in phase k + 1 (its contents are read now)
         }
         st.tl.gcnt = &g.ctl->itl[nxt];
         st.tl.glist = g.TL[nxt];
@@ -1049,7 +1122,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
         st.cl.gcap = g.clcap;
         if (!scan) {
             const int32_t s_lo = l == 0 ? 0 : g.bins[l - 1], s_hi = g.bins[l];
-            ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm, 0);
+            ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm, 0, k + 1);
         } else {
             m = g.ctl->imcnt[cur];
             tlc = g.ctl->itl[cur];
@@ -1061,7 +1134,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             const int32_t fcur = level_flag(l), fnext = level_flag(l + 1);
             const int32_t cut_next = sh_upmax[(l + 1) / g.Lg];
             if (spos < nlev && g.levlist[spos] == l + 1)  // initial candidates on l + 1
-                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm, T.nwarps() / 2);
+                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm, T.nwarps() / 2, k + 1);
             // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
             for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
                 const int i = i0 + lane;
@@ -1084,77 +1157,135 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         visits += ws[q] >= 0;
-                        if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cnt_l)) push |= 1u << q;
+                        if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cnt_l) & 1) push |= 1u << q;
                     }
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
-                    marks_add(g, st, push, ws, mbuf, mc, wsm);
+                    marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
                 }
+                upv += up_v;
                 const bool again = have && ins_finish_mover(g, it.x, up_v, cnt_l, l, fcur, fnext, cut_next);
-                enqueue_mover(g, st, again, it.x, 0, have ? 1 << it.y : 0, (int64_t)it.z * 4, wsm);
+                enqueue_ins(g, st, again, it.x, have ? 1 << it.y : 0, (int64_t)it.z * 4, -1, 0, 0, k + 1, wsm);
             }
             // chunk items: four per warp iteration, all loads of a step issued together;
             // taken from the last warp down, so that in a small round the warps
             // scanning thread-mode items and those scanning chunks are different ones
             const int crank = T.nwarps() - 1 - T.wid();
+            const int4 *lin4 = reinterpret_cast<const int4 *>(lin);
             for (int c0 = crank; c0 < clc; c0 += 4 * T.nwarps()) {
                 int4 it[4];
                 bool ok[4], in[4];
                 int32_t ws[16], lv[16];
-                int32_t upl = 0;  // lane u < 4: up-degree of item u's vertex
+                int32_t upl = 0, lol = -1, dgl = 0;  // lane u < 4: item u's vertex: up-degree, output up-list, degree
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int cu = c0 + u * T.nwarps();
                     it[u] = cu < clc ? g.CL[cur][cu] : make_int4(0, 0, 0, 0);
-                    ok[u] = cu < clc && item_ok(g, it[u], it[u].y & 31);
-                    if (lane == u && ok[u]) upl = g.up[it[u].x];
+                    const bool lst = (it[u].y & 31) == 31;
+                    ok[u] = cu < clc && (lst ? (it[u].x >= 0 && it[u].x < g.n && it[u].w >= 0 && it[u].z >= 0 &&
+                                                (int64_t)it[u].z * 4 + it[u].w <= g.lcap)
+                                             : item_ok(g, it[u], it[u].y & 31));
+                    if (lane == u && ok[u]) {
+                        upl = g.up[it[u].x];
+                        lol = g.lout[it[u].x];
+                        dgl = g.deg[it[u].x];
+                    }
+                    const int ng = lst ? (it[u].w + 3) >> 2 : (1 << (it[u].y & 31)) >> 2;
                     const int j = (it[u].y >> 5) * (kChunk / 4) + lane;
-                    in[u] = ok[u] && j < ((1 << (it[u].y & 31)) >> 2);
-                    const int4 s4 = in[u] ? pool4[it[u].z + j] : empty4();
+                    in[u] = ok[u] && j < ng;
+                    const int4 s4 = in[u] ? (lst ? lin4[it[u].z + j] : pool4[it[u].z + j]) : empty4();
                     ws[4 * u] = s4.x; ws[4 * u + 1] = s4.y; ws[4 * u + 2] = s4.z; ws[4 * u + 3] = s4.w;
                 }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) lv[q] = valid_id(g, ws[q]) ? g.level[ws[q]] : 0;
                 int cl4[4] = {0, 0, 0, 0};
-                unsigned push = 0;
+                unsigned push = 0, keep = 0;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    visits += ws[q] >= 0;
-                    if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cl4[q >> 2])) push |= 1u << q;
+                    const int r = ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cl4[q >> 2]);
+                    if (r & 1) push |= 1u << q;
+                    if (r & 2) keep |= 1u << q;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
-                marks_add(g, st, push, ws, mbuf, mc, wsm);
-                // the last chunk of a table to finish completes its mover
-                unsigned again = 0;
+                marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
+                // per item u: neighbours left on l (cnt), entries kept for the up-list
+                // (kept, with this lane's offset kex[u]); lane u < 4 then issues item u's
+                // two atomics together: room in the up-list, and the chunk count
+                int kex[4];
+                int myc = 0, mykt = 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int cnt = warp_sum(cl4[u]);
-                    const int32_t up_u = __shfl_sync(kFull, upl, u);
-                    if (lane == 0 && ok[u]) {
-                        const int lg = it[u].y & 31;
-                        const int nch = max(1, (1 << lg) / kChunk);
-                        bool last = true;
-                        int32_t total = cnt;
-                        if (nch > 1) {
-                            const unsigned long long o =
-                                atomicAdd(&g.acc[it[u].x], (1ull << 32) | (unsigned long long)(uint32_t)cnt);
-                            last = (int)(o >> 32) + 1 == nch;
-                            total = (int32_t)(uint32_t)(o & 0xffffffffull) + cnt;
-                            if (last) g.acc[it[u].x] = 0ull;
-                        }
-                        if (last && ins_finish_mover(g, it[u].x, up_u, total, l, fcur, fnext, cut_next))
-                            again |= 1u << u;
+                    const int c = warp_sum(cl4[u]);
+                    int kt;
+                    kex[u] = warp_exclusive(__popc((keep >> (4 * u)) & 0xFu), &kt);
+                    if (lane == u) {
+                        myc = c;
+                        mykt = kt;
                     }
                 }
-                again = __shfl_sync(kFull, again, 0);
                 int4 mine = it[0];
+                bool mok = ok[0];
 #pragma unroll
                 for (int u = 1; u < 4; ++u)
-                    if (lane == u) mine = it[u];
-                const bool cont = lane < 4 && ((again >> lane) & 1u);
-                enqueue_mover(g, st, cont, mine.x, 0, cont ? 1 << (mine.y & 31) : 0, (int64_t)mine.z * 4, wsm);
+                    if (lane == u) {
+                        mine = it[u];
+                        mok = ok[u];
+                    }
+                const bool mlst = (mine.y & 31) == 31;
+                int fbase = 0;
+                bool last = false;
+                int32_t total = 0;
+                if (lane < 4 && mok) {
+                    if (lol >= 0 && mykt > 0) fbase = atomicAdd(&fill_cur[mine.x], mykt);
+                    const int nch = mlst ? max(1, (mine.w + kChunk - 1) / kChunk) : max(1, (1 << (mine.y & 31)) / kChunk);
+                    last = true;
+                    total = myc;
+                    if (nch > 1) {
+                        const unsigned long long o =
+                            atomicAdd(&g.acc[mine.x], (1ull << 32) | (unsigned long long)(uint32_t)myc);
+                        last = (int)(o >> 32) + 1 == nch;
+                        total = (int32_t)(uint32_t)(o & 0xffffffffull) + myc;
+                        if (last) g.acc[mine.x] = 0ull;
+                    }
+                }
+                // the kept neighbours go to their mover's up-list
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t lo = __shfl_sync(kFull, lol, u);
+                    const int kb0 = __shfl_sync(kFull, fbase, u);
+                    if (lo < 0) continue;  // warp-uniform
+                    const unsigned kb = (keep >> (4 * u)) & 0xFu;
+                    int32_t *dst = lwr + (int64_t)lo * 4 + kb0 + kex[u];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if ((kb >> q) & 1u) *dst++ = ws[4 * u + q];
+                }
+                // the last chunk of a mover to finish completes it (lane u: item u)
+                int32_t nul = 0;  // lane u < 4: item u's new up-degree
+                bool cont = false;
+                if (last) {
+                    visits += dgl;  // a move examines the mover's neighbours: its degree
+                    upv += upl;
+                    nul = upl - total;
+                    cont = ins_finish_mover(g, mine.x, upl, total, l, fcur, fnext, cut_next);
+                    for (int p = nul; cont && lol >= 0 && (p & 3); ++p) lwr[(int64_t)lol * 4 + p] = kEmpty;
+                }
+                // a mover that keeps climbing is scanned next from its up-list, or from
+                // its table again when its list did not fit
+                int32_t mc_cap = 0;
+                int64_t moff = 0;
+                if (cont && lol < 0) {
+                    if (mlst) {
+                        mc_cap = g.cap[mine.x];
+                        moff = g.off[mine.x];
+                    } else {
+                        mc_cap = 1 << (mine.y & 31);
+                        moff = (int64_t)mine.z * 4;
+                    }
+                }
+                enqueue_ins(g, st, cont, mine.x, mc_cap, moff, (cont && lol >= 0) ? nul : -1, lol, nul, k + 1, wsm);
             }
-            marks_flush(g, st, mbuf, mc, wsm);
+            marks_flush(g, st, mbuf, mc, k + 1, wsm);
         }
         const uint64_t t_work = (g.trace && T.leader()) ? global_ns() : 0;
         stage_flush_round(g, st, 6u);
@@ -1191,9 +1322,11 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
     }
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
+    upv = warp_sum64(upv);
     if (lane == 0) {
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
+        atomicAdd(&g.ctl->st[kStUpVisits], upv);
     }
     return T.sync();
 }

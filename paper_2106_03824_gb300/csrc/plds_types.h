@@ -29,7 +29,7 @@ enum : int32_t {
 // statistics slots (Ctl::st)
 enum : int {
     kStSubmitted = 0, kStSelfLoops, kStDuplicates, kStFiltered, kStValid, kStRounds, kStMoves,
-    kStVisits, kStDlEvals, kStDlVisits, kStSlotsScanned, kStCount
+    kStVisits, kStDlEvals, kStDlVisits, kStSlotsScanned, kStUpVisits, kStCount
 };
 
 enum : int32_t { kOpInsert = 0, kOpDelete = 1 };
@@ -44,6 +44,7 @@ struct Ctl {
     int32_t tcount;              // touched vertices
     int32_t shrink_used;         // arena ints used by table shrinking
     unsigned long long grow_total;  // slots requested by growing tables
+    unsigned long long ltop[3];  // insertion: int4 units handed out of each up-list buffer
     int32_t imcnt[3];     // insertion: movers marked for a phase (phase index mod 3)
     int32_t itl[3];       // insertion: thread-mode scan items of a phase
     int32_t icl[3];       // insertion: chunk scan items of a phase
@@ -73,6 +74,8 @@ struct GraphCtx {
     int32_t test_delay_us;
     int32_t barrier_sleep_ns;
     int32_t block_cap;     // tables above this many slots get a whole block (desire-levels, rebuilds)
+    int32_t list_cap;      // insertion: chunk-scanned tables from this size on get an up-list
+    int32_t pad2;
     int64_t wait_limit_ns;
     const int32_t *upmax;  // [G]
     const int32_t *dnmin;  // [G]
@@ -98,6 +101,10 @@ struct GraphCtx {
     int32_t *bins;         // [K+1] level histogram / offsets
     int32_t *levlist;      // [K] distinct candidate levels
     unsigned long long *acc;  // [n] insertion: per mover {chunks done << 32 | neighbours left below}
+    int32_t *lbuf[3];      // insertion: up-list buffers (phase index mod 3), lcap entries each
+    int64_t lcap;
+    int32_t *lout;         // [n] insertion: a chunk-mode mover's output up-list (int4 units), -1 none
+    int32_t *lfill[2];     // [n] insertion: entries written to it so far (by phase parity)
     int4 *M[2];            // movers {v, aux, cap, -} [n]
     int4 *TL[3];           // thread-mode scan items {v, log2 cap, offset/4, aux} [n]
     int4 *CL[3];           // chunk scan items {v, chunk<<5 | log2 cap, offset/4, aux} [clcap]

@@ -35,7 +35,7 @@ class PldsStats(ctypes.Structure):
         "submitted", "self_loops", "duplicates", "filtered", "valid", "rounds", "moves", "visits",
         "dl_evals", "dl_visits", "slots_scanned", "pool_slots_used", "pool_slots_cap", "device_bytes",
         "pool_grows", "err_bits", "err_site")] + [("err_info", ctypes.c_int64 * 3)] + \
-        [(k, ctypes.c_int64) for k in ("kernel_ns", "launches")]
+        [(k, ctypes.c_int64) for k in ("kernel_ns", "launches", "up_visits")]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "err_info"}
@@ -48,9 +48,10 @@ class PldsTuning(ctypes.Structure):
                 ("load_den", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("test_delay_us", ctypes.c_int32),
                 ("trace_rounds", ctypes.c_int32), ("barrier_sleep_ns", ctypes.c_int32),
-                ("block_cap", ctypes.c_int32), ("track_orientation", ctypes.c_int32)]
+                ("block_cap", ctypes.c_int32), ("track_orientation", ctypes.c_int32),
+                ("list_cap", ctypes.c_int32)]
 
-    KNOBS = ("thread_max_cap", "block_cap", "load_num", "load_den")
+    KNOBS = ("thread_max_cap", "block_cap", "load_num", "load_den", "list_cap")
 
     def knobs(self) -> dict:
         return {k: int(getattr(self, k)) for k in self.KNOBS}
@@ -358,7 +359,7 @@ class PLDSSet:
         return rc
 
     def tune(self, **knobs):
-        """Apply thread_max_cap / block_cap / load_num / load_den to every graph."""
+        """Apply thread_max_cap / block_cap / load_num / load_den / list_cap to every graph."""
         t = PldsTuning()
         for k, v in knobs.items():
             setattr(t, k, int(v))

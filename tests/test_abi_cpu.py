@@ -75,18 +75,19 @@ def test_tune_search_finds_the_minimum_of_a_separable_cost(lib):
                 + 10 * abs(k["load_num"] / k["load_den"] - 0.625))
 
     best, n = P.tune_search(cost)
-    assert best == {"thread_max_cap": 8, "block_cap": 8192, "load_num": 5, "load_den": 8}
+    assert best == {"thread_max_cap": 8, "block_cap": 8192, "load_num": 5, "load_den": 8, "list_cap": 256}
     assert n == len(seen) == len(set(seen))
-    for t, b, ln, ld in seen:
+    for t, b, ln, ld, lc in seen:
         assert t in (4, 8, 16, 32, 64) and b in (1024, 2048, 4096, 8192, 16384)
-        assert (ln, ld) in ((1, 2), (5, 8), (3, 4), (7, 8))
+        assert (ln, ld) in ((1, 2), (5, 8), (3, 4), (7, 8)) and lc in (128, 256, 1024, 1 << 30)
 
 
 def test_tune_search_budget_and_failure(lib):
     calls = []
     best, n = P.tune_search(lambda k: calls.append(k) or 1.0, max_trials=3)
     assert n == 3 and len(calls) == 3
-    assert best == {"thread_max_cap": 16, "block_cap": 4096, "load_num": 3, "load_den": 4}  # flat: defaults kept
+    assert best == {"thread_max_cap": 16, "block_cap": 4096, "load_num": 3, "load_den": 4,
+                    "list_cap": 256}  # flat: defaults kept
     with pytest.raises(P.PldsError) as ex:
         P.tune_search(lambda k: -1.0)
     assert ex.value.code == P.PLDS_EINTERNAL

@@ -125,8 +125,9 @@ def test_set_knobs_never_change_results_and_autotune(P):
     assert best["thread_max_cap"] in (4, 8, 16, 32, 64)
     assert best["block_cap"] in (1024, 2048, 4096, 8192, 16384)
     assert (best["load_num"], best["load_den"]) in ((1, 2), (5, 8), (3, 4), (7, 8))
+    assert best["list_cap"] in (128, 256, 1024, 1 << 30)
     extreme = P.PLDSSet(ns)
-    extreme.tune(thread_max_cap=4, block_cap=4, load_num=1, load_den=2)
+    extreme.tune(thread_max_cap=4, block_cap=4, load_num=1, load_den=2, list_cap=32)
     for r, (e, o) in enumerate(dev):
         for S in (tuned, extreme):
             S.update(e, o)

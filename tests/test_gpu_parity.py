@@ -246,9 +246,9 @@ def test_tuning_never_changes_results(P):
     n = 1 << 13
     e = W.rmat(13, 16, seed=5)
     ref = None
-    for tune in (dict(), dict(thread_max_cap=4, load_num=1, load_den=2, block_threads=256, block_cap=4),
+    for tune in (dict(), dict(thread_max_cap=4, load_num=1, load_den=2, block_threads=256, block_cap=4, list_cap=8),
                  dict(thread_max_cap=64, load_num=7, load_den=8, block_threads=512, blocks_per_sm=2,
-                      block_cap=16384)):
+                      block_cap=16384, list_cap=1 << 30)):
         g = P.PLDS(n)
         if tune:
             g.set_tuning(**tune)
