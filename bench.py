@@ -55,6 +55,20 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def whole_job(dist, updates: float, seconds: float, device: str):
+    """The whole-job figures of a replicas run: the updates of every rank and the
+    slowest rank's time (one collective each; the identity without a process
+    group).  Returns (total updates, max seconds)."""
+    if dist is None:
+        return updates, seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(u.item()), float(t.item())
+
+
 def algo_bytes(s: dict) -> int:
     """Algorithmic bytes of one batch kernel launch: 8 B per submitted edge; 64 B per
     applied update (2 probes + 2 slot writes of 4 B, 6 counter read-modify-writes of
@@ -710,16 +724,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = g.stats()["launches"] - launches0
     g.close()
-    t_max = ms
-    upd_all = upd
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([float(upd)], device="cuda")
-        dist.all_reduce(u)
-        upd_all = int(u.item())
-    value = upd_all / (t_max / 1e3)
+    upd_all, t_max_s = whole_job(dist, upd, ms / 1e3, "cuda")
+    t_max = t_max_s * 1e3
+    value = upd_all / t_max_s
 
     # roofline of the batch kernel: algorithmic bytes / event-timed kernel duration
     kern_ns = sum(r["kernel_ns"] for r in recs)
@@ -756,11 +763,8 @@ def main():
         torch.cuda.synchronize()
         dt2 = time.perf_counter() - t0
         g2.close()
-        if dist:
-            t = torch.tensor([dt2], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt2 = float(t.item())
-        e2e = {"value": upd2 * world / dt2, "unit": UNIT, "h2d_bytes_per_step": 8 * upd2 / args.steps,
+        upd2_all, dt2 = whole_job(dist, upd2, dt2, "cuda")
+        e2e = {"value": upd2_all / dt2, "unit": UNIT, "h2d_bytes_per_step": 8 * upd2 / args.steps,
                "d2h_bytes_per_step": 8 * n}
 
     # per-batch latency of the timed steps (kernel time of each call)

@@ -276,6 +276,8 @@ int plds_trace(plds_t *h, int32_t *out, int32_t cap);
  *     calls; an id outside [0, n[i]) rejects the round before graph i changes.
  *   plds_set_graph: the handle of graph i, owned by the set, for queries and
  *     statistics (the last round's counts of both halves, summed).
+ * The graphs of a set start with thread_max_cap = 64 (a block per graph scans
+ * small tables better one thread each); plds_set_tune / plds_set_autotune change it.
  */
 typedef struct plds_set plds_set_t;
 plds_set_t *plds_set_create(int32_t count, const int32_t *n, double delta, double lambda,

@@ -1536,6 +1536,8 @@ extern "C" plds_set_t *plds_set_create(int32_t count, const int32_t *n, double d
             set_status(rc);
             return nullptr;
         }
+        // one block per graph: tables up to 64 slots are scanned better by one thread
+        h->tune.thread_max_cap = 64;
         s->g.push_back(h);
     }
     s->owner = s->g[0];
