@@ -1394,6 +1394,28 @@ __device__ __forceinline__ int warp_window_find(const int32_t *h, int lo, int hi
     return m ? __shfl_sync(kFull, found, __ffs(m) - 1) : -1;
 }
 
+// The levels of the neighbours in table t4[0..ng) seen by one lane of a warp or one
+// thread of a block (groups start, start + stride, ...), four 4-slot groups per step
+// so that 16 level loads are in flight: f(level) for every neighbour.
+template <class F>
+__device__ __forceinline__ void scan_levels(const GraphCtx &g, const int4 *t4, int32_t ng, int start, int stride,
+                                            F f) {
+    for (int j0 = start; j0 < ng; j0 += 4 * stride) {
+        int32_t ws[16], lv[16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * stride;
+            const int4 q = j < ng ? t4[j] : empty4();
+            ws[4 * u] = q.x; ws[4 * u + 1] = q.y; ws[4 * u + 2] = q.z; ws[4 * u + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) lv[k] = ws[k] >= 0 ? g.level[ws[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (lv[k] >= 0) f(lv[k]);
+    }
+}
+
 __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
                                      int32_t *hist) {
     if (lw < 2) return 0;
@@ -1404,15 +1426,7 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
     const int32_t xmax = lw - 2;
     for (int k = lane; k < G; k += 32) hist[k] = 0;
     __syncwarp();
-    for (int j = lane; j < ng; j += 32) {
-        const int4 q = t4[j];
-        const int32_t a = q.x >= 0 ? g.level[q.x] : -1, b = q.y >= 0 ? g.level[q.y] : -1;
-        const int32_t c = q.z >= 0 ? g.level[q.z] : -1, d = q.w >= 0 ? g.level[q.w] : -1;
-        if (a >= 0) atomicAdd(&hist[a / Lg], 1);
-        if (b >= 0) atomicAdd(&hist[b / Lg], 1);
-        if (c >= 0) atomicAdd(&hist[c / Lg], 1);
-        if (d >= 0) atomicAdd(&hist[d / Lg], 1);
-    }
+    scan_levels(g, t4, ng, lane, 32, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
     __syncwarp();
     const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
     __syncwarp();
@@ -1423,16 +1437,10 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
         const int32_t lo = max(a, hi - (kWindow - 1));
         for (int k = lane; k < kWindow + 1; k += 32) hist[k] = 0;
         __syncwarp();
-        for (int j = lane; j < ng; j += 32) {
-            const int4 q = t4[j];
-            int32_t lu[4] = {q.x >= 0 ? g.level[q.x] : -1, q.y >= 0 ? g.level[q.y] : -1,
-                             q.z >= 0 ? g.level[q.z] : -1, q.w >= 0 ? g.level[q.w] : -1};
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (lu[s] > hi) atomicAdd(&hist[kWindow], 1);
-                else if (lu[s] >= lo) atomicAdd(&hist[lu[s] - lo], 1);
-            }
-        }
+        scan_levels(g, t4, ng, lane, 32, [&](int32_t x) {
+            if (x > hi) atomicAdd(&hist[kWindow], 1);
+            else if (x >= lo) atomicAdd(&hist[x - lo], 1);
+        });
         __syncwarp();
         const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
         __syncwarp();
@@ -1453,15 +1461,7 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     const int32_t xmax = lw - 2;
     for (int k = threadIdx.x; k < G; k += blockDim.x) hist[k] = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < ng; j += blockDim.x) {
-        const int4 q = t4[j];
-        const int32_t a = q.x >= 0 ? g.level[q.x] : -1, b = q.y >= 0 ? g.level[q.y] : -1;
-        const int32_t c = q.z >= 0 ? g.level[q.z] : -1, d = q.w >= 0 ? g.level[q.w] : -1;
-        if (a >= 0) atomicAdd(&hist[a / Lg], 1);
-        if (b >= 0) atomicAdd(&hist[b / Lg], 1);
-        if (c >= 0) atomicAdd(&hist[c / Lg], 1);
-        if (d >= 0) atomicAdd(&hist[d / Lg], 1);
-    }
+    scan_levels(g, t4, ng, threadIdx.x, blockDim.x, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
     __syncthreads();
     if (threadIdx.x < 32) {
         const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
@@ -1477,16 +1477,10 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
         const int32_t lo = max(a, hi - (kWindow - 1));
         for (int k = threadIdx.x; k < kWindow + 1; k += blockDim.x) hist[k] = 0;
         __syncthreads();
-        for (int j = threadIdx.x; j < ng; j += blockDim.x) {
-            const int4 q = t4[j];
-            int32_t lu[4] = {q.x >= 0 ? g.level[q.x] : -1, q.y >= 0 ? g.level[q.y] : -1,
-                             q.z >= 0 ? g.level[q.z] : -1, q.w >= 0 ? g.level[q.w] : -1};
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (lu[s] > hi) atomicAdd(&hist[kWindow], 1);
-                else if (lu[s] >= lo) atomicAdd(&hist[lu[s] - lo], 1);
-            }
-        }
+        scan_levels(g, t4, ng, threadIdx.x, blockDim.x, [&](int32_t x) {
+            if (x > hi) atomicAdd(&hist[kWindow], 1);
+            else if (x >= lo) atomicAdd(&hist[x - lo], 1);
+        });
         __syncthreads();
         if (threadIdx.x < 32) {
             const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
