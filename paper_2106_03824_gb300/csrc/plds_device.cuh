@@ -1416,6 +1416,18 @@ __device__ __forceinline__ void scan_levels(const GraphCtx &g, const int4 *t4, i
     }
 }
 
+// Sum of h[lo..hi] (at most 256 entries) over a warp.
+__device__ __forceinline__ int warp_range_sum(const int32_t *h, int lo, int hi) {
+    int s = 0;
+    for (int k = lo + lane_id(); k <= hi; k += 32) s += h[k];
+    return warp_sum(s);
+}
+
+// Desire-level of w on level lw (Definition): the largest l' < lw whose level below
+// has at least dnmin[gn(l'-1)] neighbours on it or above, found from a histogram of
+// the neighbours' groups and then of the levels in the best group.  The first scan
+// also counts the 256 levels just below lw - 1 one by one: when the best group lies
+// in that window (the common case) no second scan is needed.
 __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
                                      int32_t *hist) {
     if (lw < 2) return 0;
@@ -1424,17 +1436,36 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
     const int32_t ng = g.cap[w] >> 2;
     const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
     const int32_t xmax = lw - 2;
+    const int32_t w0 = max(0, xmax - (kWindow - 1));
+    int32_t *win = hist + G;  // levels w0..xmax one by one, win[kWindow]: above xmax
+    const bool one = G + kWindow + 1 <= kWarpHist;
     for (int k = lane; k < G; k += 32) hist[k] = 0;
+    if (one)
+        for (int k = lane; k <= kWindow; k += 32) win[k] = 0;
     __syncwarp();
-    scan_levels(g, t4, ng, lane, 32, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
+    if (one) {
+        scan_levels(g, t4, ng, lane, 32, [&](int32_t x) {
+            atomicAdd(&hist[x / Lg], 1);
+            if (x > xmax) atomicAdd(&win[kWindow], 1);
+            else if (x >= w0) atomicAdd(&win[x - w0], 1);
+        });
+    } else {
+        scan_levels(g, t4, ng, lane, 32, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
+    }
     __syncwarp();
     const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
     __syncwarp();
     if (best < 0) return 0;
     const int32_t need = sh_dnmin[best], a = best * Lg;
     int32_t hi = min((best + 1) * Lg - 1, xmax);
+    if (one && a >= w0) {  // the best group's levels were counted by the first scan
+        const int above = win[kWindow] + warp_range_sum(win, hi + 1 - w0, xmax - w0);
+        const int found = warp_window_find(win + (a - w0), a, hi, above, need);
+        return found >= 0 ? found + 1 : a + 1;  // a + 1 unreachable: cnt(a) >= need holds
+    }
     for (;;) {
         const int32_t lo = max(a, hi - (kWindow - 1));
+        __syncwarp();
         for (int k = lane; k < kWindow + 1; k += 32) hist[k] = 0;
         __syncwarp();
         scan_levels(g, t4, ng, lane, 32, [&](int32_t x) {
@@ -1450,8 +1481,6 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
     }
 }
 
-// The same computation by the whole block for a large table; hist has
-// max(G, kWindow + 1) ints of block shared memory, *res one int.
 __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
                                       int32_t *hist, int32_t *res) {
     if (lw < 2) return 0;
@@ -1459,9 +1488,22 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     const int32_t ng = g.cap[w] >> 2;
     const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
     const int32_t xmax = lw - 2;
+    const int32_t w0 = max(0, xmax - (kWindow - 1));
+    int32_t *win = hist + G;  // as in warp_desire_level: one scan when the answer is near
+    const bool one = G + kWindow + 1 <= kWarpHist;
     for (int k = threadIdx.x; k < G; k += blockDim.x) hist[k] = 0;
+    if (one)
+        for (int k = threadIdx.x; k <= kWindow; k += blockDim.x) win[k] = 0;
     __syncthreads();
-    scan_levels(g, t4, ng, threadIdx.x, blockDim.x, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
+    if (one) {
+        scan_levels(g, t4, ng, threadIdx.x, blockDim.x, [&](int32_t x) {
+            atomicAdd(&hist[x / Lg], 1);
+            if (x > xmax) atomicAdd(&win[kWindow], 1);
+            else if (x >= w0) atomicAdd(&win[x - w0], 1);
+        });
+    } else {
+        scan_levels(g, t4, ng, threadIdx.x, blockDim.x, [&](int32_t x) { atomicAdd(&hist[x / Lg], 1); });
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
         const int best = warp_best_group(hist, G, xmax / Lg, sh_dnmin);
@@ -1473,6 +1515,17 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     if (best < 0) return 0;
     const int32_t need = sh_dnmin[best], a = best * Lg;
     int32_t hi = min((best + 1) * Lg - 1, xmax);
+    if (one && a >= w0) {  // the best group's levels were counted by the first scan
+        if (threadIdx.x < 32) {
+            const int above = win[kWindow] + warp_range_sum(win, hi + 1 - w0, xmax - w0);
+            const int found = warp_window_find(win + (a - w0), a, hi, above, need);
+            if (threadIdx.x == 0) *res = found;
+        }
+        __syncthreads();
+        const int found = *res;
+        __syncthreads();
+        return found >= 0 ? found + 1 : a + 1;  // a + 1 unreachable: cnt(a) >= need holds
+    }
     for (;;) {
         const int32_t lo = max(a, hi - (kWindow - 1));
         for (int k = threadIdx.x; k < kWindow + 1; k += blockDim.x) hist[k] = 0;
