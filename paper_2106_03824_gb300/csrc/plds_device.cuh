@@ -33,6 +33,7 @@ __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(volatile
 // Teams
 // ---------------------------------------------------------------------------
 struct GridTeam {
+    static constexpr bool kGrid = true;  // barriers cost a round trip to L2: fetch at the barrier
     Ctl *ctl;
     int64_t limit_ns;
     int32_t sleep_ns;
@@ -50,7 +51,28 @@ struct GridTeam {
     // carry the other threads' writes and reads.
     __device__ bool sync() {
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) arrive_wait();
+        __syncthreads();
+        return ld_volatile(&ctl->err) == 0;
+    }
+    // The same barrier, after which warp 0 runs fetch(lane) -- the loads the next
+    // phase starts with, written to shared memory -- while lane 0 reads the error
+    // word into *ok_slot: one round of loads for the block instead of a read of
+    // the error word by every thread followed by the phase's own first loads.
+    template <class F>
+    __device__ __forceinline__ bool sync_fetch(F fetch, int32_t *ok_slot) {
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) arrive_wait();
+            __syncwarp();  // orders warp 0's loads after the acquire
+            if (threadIdx.x == 0) *ok_slot = ld_volatile(&ctl->err);
+            fetch((int)threadIdx.x);
+        }
+        __syncthreads();
+        return *ok_slot == 0;
+    }
+    __device__ void arrive_wait() {
+        {
             unsigned long long *cnt = &ctl->bar_arrivals;
             unsigned long long a;
             asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(a) : "l"(cnt) : "memory");
@@ -74,12 +96,11 @@ struct GridTeam {
                 if (sleep_ns) __nanosleep(sleep_ns);
             }
         }
-        __syncthreads();
-        return ld_volatile(&ctl->err) == 0;
     }
 };
 
 struct BlockTeam {
+    static constexpr bool kGrid = false;
     Ctl *ctl;
     __device__ int tid() const { return threadIdx.x; }
     __device__ int nthreads() const { return blockDim.x; }
@@ -697,19 +718,23 @@ __device__ __forceinline__ void stage_flush(const GraphCtx &g, const Stage<V> &s
 constexpr int kStageF = 2048, kStageTL = 1024, kStageCL = 2048, kStagePK = 1024;
 
 // Shared-memory staging of one round: frontier / recompute list, thread-mode and
-// chunk scan items, pending entries, and the block's mover count.
+// chunk scan items, pending entries, the block's mover count, and what warp 0
+// fetches for the next phase while it passes the team barrier (ph4: one item per
+// warp; phs: words).
 struct RoundStage {
     Stage<int32_t> f;
     Stage<int4> tl, cl, pk;
     int32_t *movers;  // shared mover count of the block
     int32_t *bmin;    // shared minimum pending level of the block
     int32_t *tmp;
+    int4 *ph4;
+    int32_t *phs;
 };
 
 // Shared ints of a staging area whose capacities are the defaults >> shift
 // (a block-sized team, alone on its graph, needs far less room than a grid).
 __host__ __device__ constexpr int stage_ints(int shift) {
-    return 16 + (kStageF >> shift) + 4 * ((kStageTL >> shift) + (kStageCL >> shift) + (kStagePK >> shift));
+    return 128 + (kStageF >> shift) + 4 * ((kStageTL >> shift) + (kStageCL >> shift) + (kStagePK >> shift));
 }
 
 // Lay out the staging area (stage_ints(shift) ints of shared memory, 16-byte aligned).
@@ -717,8 +742,10 @@ __device__ __forceinline__ RoundStage stage_setup(int32_t *base, int shift) {
     RoundStage st{};
     const int cf = kStageF >> shift, ct = kStageTL >> shift, cc = kStageCL >> shift, cp = kStagePK >> shift;
     int32_t *hdr = base;
-    st.f.buf = base + 16;
-    st.tl.buf = reinterpret_cast<int4 *>(base + 16 + cf);
+    st.ph4 = reinterpret_cast<int4 *>(base + 32);  // 16 int4
+    st.phs = base + 96;                             // 32 ints
+    st.f.buf = base + 128;
+    st.tl.buf = reinterpret_cast<int4 *>(base + 128 + cf);
     st.cl.buf = st.tl.buf + ct;
     st.pk.buf = st.cl.buf + cc;
     st.f.hdr = hdr;
@@ -840,8 +867,8 @@ __device__ __forceinline__ void enqueue_mover(const GraphCtx &g, const RoundStag
 __device__ __forceinline__ void enqueue_ins(const GraphCtx &g, const RoundStage &st, bool is_mover, int32_t v,
                                             int32_t c, int64_t off, int32_t ilen, int32_t ioff4, int32_t rsize,
                                             int k1, int32_t *wsm) {
-    const int abuf = k1 % 3;  // k1: index of the phase that scans these movers
 
+    const int abuf = k1 % 3;
     const int lane = lane_id();
     const unsigned mm = __ballot_sync(kFull, is_mover);
     if (mm == 0) return;
@@ -1108,6 +1135,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
         int32_t *fill_cur = g.lfill[k & 1];  // reset when this phase's movers were queued
         const uint64_t t_phase = (g.trace && T.leader()) ? global_ns() : 0;
         int32_t tlc = 0, clc = 0, m = 0;
+        bool has_init = false;
         if (T.leader()) {  // the lists of phase k - 1 are done with; phase k + 1 fills them next
             g.ctl->itl[old] = 0;
             g.ctl->icl[old] = 0;
@@ -1124,17 +1152,31 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             const int32_t s_lo = l == 0 ? 0 : g.bins[l - 1], s_hi = g.bins[l];
             ins_test_initial(T, g, st, s_lo, s_hi, l, sh_upmax[l / g.Lg], wsm, 0, k + 1);
         } else {
-            m = g.ctl->imcnt[cur];
-            tlc = g.ctl->itl[cur];
-            clc = g.ctl->icl[cur];
+            // counts, next initial-candidate level and its range (fetched at a grid barrier)
+            int32_t s_lo, s_hi;
+            if constexpr (Team::kGrid) {
+                m = st.phs[1];
+                tlc = st.phs[2];
+                clc = st.phs[3];
+                has_init = st.phs[4] == l + 1;
+                s_lo = st.phs[5];
+                s_hi = st.phs[6];
+            } else {
+                m = g.ctl->imcnt[cur];
+                tlc = g.ctl->itl[cur];
+                clc = g.ctl->icl[cur];
+                has_init = spos < nlev && g.levlist[spos] == l + 1;
+                s_lo = has_init ? g.bins[l] : 0;
+                s_hi = has_init ? g.bins[l + 1] : 0;
+            }
             if (T.leader()) {
-                g.ctl->st[kStRounds] += 1;
-                g.ctl->st[kStMoves] += (unsigned long long)m;
+                atomicAdd(&g.ctl->st[kStRounds], 1ull);
+                atomicAdd(&g.ctl->st[kStMoves], (unsigned long long)m);
             }
             const int32_t fcur = level_flag(l), fnext = level_flag(l + 1);
             const int32_t cut_next = sh_upmax[(l + 1) / g.Lg];
-            if (spos < nlev && g.levlist[spos] == l + 1)  // initial candidates on l + 1
-                ins_test_initial(T, g, st, g.bins[l], g.bins[l + 1], l + 1, cut_next, wsm, T.nwarps() / 2, k + 1);
+            if (has_init)  // initial candidates on l + 1
+                ins_test_initial(T, g, st, s_lo, s_hi, l + 1, cut_next, wsm, T.nwarps() / 2, k + 1);
             // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
             for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
                 const int i = i0 + lane;
@@ -1179,7 +1221,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int cu = c0 + u * T.nwarps();
-                    it[u] = cu < clc ? g.CL[cur][cu] : make_int4(0, 0, 0, 0);
+                    it[u] = cu < clc ? ((Team::kGrid && cu == crank) ? st.ph4[threadIdx.x >> 5] : g.CL[cur][cu]) : make_int4(0, 0, 0, 0);
                     const bool lst = (it[u].y & 31) == 31;
                     ok[u] = cu < clc && (lst ? (it[u].x >= 0 && it[u].x < g.n && it[u].w >= 0 && it[u].z >= 0 &&
                                                 (int64_t)it[u].z * 4 + it[u].w <= g.lcap)
@@ -1293,7 +1335,42 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             atomicAdd(&g.ctl->imcnt[nxt], *st.movers);
             *st.movers = 0;
         }
-        if (!T.sync()) return false;
+        // the level the next phase scans if it has movers, and its initial-candidate
+        // entry; warp 0 fetches them with the next phase's counts and each warp's
+        // first chunk item while it passes the barrier
+        int spos2 = spos;
+        int32_t l2 = l;
+        if (scan) {
+            if (has_init) ++spos2;
+            ++l2;
+        }
+        bool passed;
+        if constexpr (Team::kGrid) {
+            const int4 *cl_next = g.CL[nxt];
+            passed = T.sync_fetch(
+                [&](int ln) {
+                    if (ln < (int)(blockDim.x >> 5)) {  // warp ln of the block: its first chunk item
+                        const int cr = T.nwarps() - 1 - (T.wid() + ln);
+                        st.ph4[ln] = cr < g.clcap ? cl_next[cr] : make_int4(0, 0, 0, 0);
+                    } else if (ln == 16) {
+                        st.phs[1] = g.ctl->imcnt[nxt];
+                    } else if (ln == 17) {
+                        st.phs[2] = g.ctl->itl[nxt];
+                    } else if (ln == 18) {
+                        st.phs[3] = g.ctl->icl[nxt];
+                    } else if (ln == 19) {
+                        st.phs[4] = spos2 < nlev ? g.levlist[spos2] : kInf;
+                    } else if (ln == 20) {
+                        st.phs[5] = l2 < g.K ? g.bins[l2] : 0;
+                    } else if (ln == 21) {
+                        st.phs[6] = l2 < g.K ? g.bins[l2 + 1] : 0;
+                    }
+                },
+                st.phs);
+        } else {
+            passed = T.sync();
+        }
+        if (!passed) return false;
         if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
             int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
             const uint64_t t_end = global_ns();
@@ -1303,11 +1380,9 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
         }
         // the next phase: the movers of l + 1 (after a scan) or of l (after a test),
         // else the initial candidates of the next level that has some
-        if (scan) {
-            if (spos < nlev && g.levlist[spos] == l + 1) ++spos;
-            ++l;
-        }
-        if (g.ctl->imcnt[nxt] > 0) {
+        spos = spos2;
+        l = l2;
+        if (Team::kGrid ? st.phs[1] > 0 : g.ctl->imcnt[nxt] > 0) {
             scan = true;
             continue;
         }
