@@ -89,7 +89,8 @@ typedef struct plds_tuning {
     int32_t trace_rounds;     /* diagnostics: 1 = record one line per level round (plds_trace) */
     int32_t barrier_sleep_ns; /* pause between polls of a grid-barrier wait (0 = default 32, -1 = none) */
     int32_t block_cap;        /* tables above this many slots get a whole block for desire-levels
-                                 and rebuilds, smaller ones a warp (0 = default 4096, else >= 4) */
+                                 and rebuilds, smaller ones a warp (0 = default: 1024 for a
+                                 handle, 4096 for the graphs of a set; else >= 4) */
     int32_t track_orientation; /* 1 = every plds_batch_insert / plds_batch_delete call saves the
                                   levels at its start (4n bytes of device memory and one copy)
                                   so that plds_flips / plds_oriented_updates can report it */

@@ -370,7 +370,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.thread_max_cap = h->tune.thread_max_cap > 0 ? h->tune.thread_max_cap : 16;
     g.load_num = h->tune.load_num > 0 ? h->tune.load_num : 3;
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
-    g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 4096;
+    g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 1024;
     g.list_cap = h->tune.list_cap > 0 ? h->tune.list_cap : 256;
     g.wait_limit_ns = h->wait_limit_ns;
     g.test_delay_us = h->tune.test_delay_us;
@@ -1536,8 +1536,10 @@ extern "C" plds_set_t *plds_set_create(int32_t count, const int32_t *n, double d
             set_status(rc);
             return nullptr;
         }
-        // one block per graph: tables up to 64 slots are scanned better by one thread
+        // one block per graph: tables up to 64 slots are scanned better by one thread,
+        // and a whole block pays off only for tables above 4096 slots
         h->tune.thread_max_cap = 64;
+        h->tune.block_cap = 4096;
         s->g.push_back(h);
     }
     s->owner = s->g[0];
