@@ -43,7 +43,7 @@ UNIT = "updates/s"
 # dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": "30c3634f131942d4", "dram_per_algo_byte": 0.2278,
+NCU_TRAFFIC = {"kernel_sha": "b311bada918cc187", "dram_per_algo_byte": 0.2269,
                "capture": "ncu DRAM counters of every k_batch_grid launch of the R-MAT 20 Ins and Del protocols"}
 
 

@@ -867,8 +867,7 @@ __device__ __forceinline__ void enqueue_mover(const GraphCtx &g, const RoundStag
 __device__ __forceinline__ void enqueue_ins(const GraphCtx &g, const RoundStage &st, bool is_mover, int32_t v,
                                             int32_t c, int64_t off, int32_t ilen, int32_t ioff4, int32_t rsize,
                                             int k1, int32_t *wsm) {
-
-    const int abuf = k1 % 3;
+    const int abuf = k1 % 3;  // k1: index of the phase that scans these movers
     const int lane = lane_id();
     const unsigned mm = __ballot_sync(kFull, is_mover);
     if (mm == 0) return;
@@ -934,11 +933,7 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
         const unsigned peers = __match_any_sync(kFull, lx);  // lanes with the same level add once
         if (i < tc && lane_id() == __ffs(peers) - 1) atomicAdd(&g.bins[lx], __popc(peers));
     }
-    if (T.leader()) {
-        g.ctl->mcnt[0] = 0;
-        g.ctl->slevel[0] = -1;
-        g.ctl->spos[0] = 0;
-    }
+    if (T.leader()) g.ctl->mcnt[0] = 0;
     if (!T.sync()) return false;
     if (T.bid() == 0) {
         int run = 0, runl = 0;

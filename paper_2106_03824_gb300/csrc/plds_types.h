@@ -38,7 +38,6 @@ enum : int32_t { kOpInsert = 0, kOpDelete = 1 };
 struct Ctl {
     unsigned long long bar_arrivals;  // grid barrier: arrivals since launch (never reset within one)
     int32_t err;          // kErr* bits
-    int32_t rounds_done;  // loop guard
     unsigned long long ucount;   // unique canonical keys
     unsigned long long vcount;   // valid (applied) keys
     int32_t tcount;              // touched vertices
@@ -51,8 +50,6 @@ struct Ctl {
     int32_t mcnt[2];      // table growth / deletion movers
     int32_t tlcnt[2];     // thread-mode movers
     int32_t clcnt[2];     // chunk items
-    int32_t slevel[2];    // insertion round state: current level
-    int32_t spos[2];      // insertion round state: next entry of the level list
     int32_t nlev;         // number of distinct initial-candidate levels
     int32_t pcnt[2];      // deletion pending list sizes
     int32_t rcnt[2];      // deletion recompute list sizes
