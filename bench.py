@@ -214,6 +214,17 @@ def cpu_sample(scale, ins, sample_batch=500_000):
                       f"full 10^6-edge batch takes minutes)"}
 
 
+def plain_config(args, n: int, m: int, world: int) -> dict:
+    """The workload of the default (plain-form) bench line; the reference arm reports the same."""
+    return {"workload": f"rmat{args.scale}_ef16_B{args.batch:.0e}_ins_del_cycle".replace("+0", ""),
+            "graph": f"R-MAT scale {args.scale}, (.57,.19,.19,.05), edge factor 16, symmetrised, deduplicated",
+            "n": n, "m": m, "batch": args.batch, "delta": 0.4, "lambda": 3,
+            "stream": "Ins all edges from empty, then Del all edges (cyclic)",
+            "form": "plain: one synchronous launch sequence per batch",
+            "l2": "no flush: graph state (~1 GB adjacency + arrays) is larger than the 129 MB L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -243,10 +254,12 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"rmat{args.scale}_ef16_ins_del_cycle", "batch": b,
-                       "note": "sequential CPU oracle; each step one Ins batch of the same stream"},
+            "config": plain_config(args, 1 << args.scale, int(e.shape[0]), int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} Ins batches of {b} edges after {args.warmup} warm-up"},
+                             "sample": f"the sequential CPU oracle as it stands, on 1 host core: {args.steps} "
+                                       f"consecutive Ins batches of {b} edges of the same stream from the empty "
+                                       f"graph, after {args.warmup} warm-up batches (a full {args.batch}-edge "
+                                       f"batch takes the oracle minutes)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -797,13 +810,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale}_ef16_B{args.batch:.0e}_ins_del_cycle".replace("+0", ""),
-                   "graph": f"R-MAT scale {args.scale}, (.57,.19,.19,.05), edge factor 16, symmetrised, deduplicated",
-                   "n": n, "m": int(e.shape[0]), "batch": args.batch, "delta": 0.4, "lambda": 3,
-                   "stream": "Ins all edges from empty, then Del all edges (cyclic)",
-                   "form": "plain: one synchronous launch sequence per batch",
-                   "l2": "no flush: graph state (~1 GB adjacency + arrays) is larger than the 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": plain_config(args, n, int(e.shape[0]), world),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
