@@ -195,6 +195,18 @@ def test_parameter_grid_every_batch(P, delta, lam, heuristic):
     """Other points of the experiments' delta / lambda grid, and the heuristic
     coefficient 1.1: Chung-Lu n = 5000, Ins then Del batches, equal to the oracle
     after every batch (tables included)."""
+    _grid_case(P, delta, lam, heuristic)
+
+
+def test_many_groups_every_batch(P):
+    """delta = 0.03 at n = 5000: 290 groups of 1156 levels, so the desire-level's
+    group and window histograms no longer share one warp's scratch and every
+    evaluation takes its two-scan path; equal to the oracle after every batch."""
+    assert O.tables(5000, 0.03, 3.0)["G"] == 290
+    _grid_case(P, 0.03, 3.0, False)
+
+
+def _grid_case(P, delta, lam, heuristic):
     n = 5000
     e = W.chung_lu(n, 30_000, 2.3, seed=31)
     flags = O.HEURISTIC if heuristic else 0
