@@ -100,6 +100,7 @@ def opt_levels_per_group(m: int, delta: float = 0.4) -> int:
 
 
 HEURISTIC = 1  # Invariant 1's coefficient 2 + 3/lambda replaced by 1.1
+JUMP = 2  # insertion violators move straight to their targets (the experiments' variant)
 
 
 def tables(n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0, flags: int = 0):

@@ -11,7 +11,9 @@
  *   - Levels, groups, Invariants 1 and 2, up / up* degrees, desire-level:
  *     Section "Detailed PLDS Algorithm" (Invariants 1-2, Definition of desire-level).
  *   - Update(B) = insertions then deletions: Algorithm 1.
- *   - RebalanceInsertions: Algorithm 2 (level-by-level, move violators up one level).
+ *   - RebalanceInsertions: Algorithm 2 (level-by-level, move violators up one level);
+ *     with ORC_JUMP, the implementation variant of Section "Experiments" that moves
+ *     each violator straight to a desire-level computed for it (see jump_target).
  *   - RebalanceDeletions: Algorithm 3, with the desire-level computed straight from
  *     its Definition (a downward linear scan testing both invariants), not with
  *     Algorithm 4's doubling search, so the device search is checked against a
@@ -184,6 +186,17 @@ typedef struct {
 /* flags: ORC_HEURISTIC replaces Invariant 1's coefficient 2 + 3/lambda by 1.1, the
    experiments' "heuristic parameters" (their efficiency bounds no longer hold). */
 #define ORC_HEURISTIC 1
+/* flags: ORC_JUMP takes the exact reading of the experiments' insertion variant
+   ("a filter and sort that computes the desire-level of the vertices moved up"
+   instead of moving them level by level): each round takes the lowest level l that
+   holds a violator of Invariant 1, and every violator on l moves at once to its own
+   target, the lowest level above l on which it would satisfy Invariant 1 with all
+   other vertices where they are (jump_target).  Its levels equal Algorithm 2's:
+   level assignments at or above the batch's starting levels under which every
+   vertex satisfies Invariant 1 are closed under the pointwise minimum, so a least
+   one exists; counts only grow as levels rise, so neither procedure moves a vertex
+   past it, and both stop only when no vertex violates.  Rounds and moves differ. */
+#define ORC_JUMP 2
 
 static int build_tables(orc_tables *T, int32_t n, double delta, double lambda, int32_t lg_override,
                         int32_t flags) {
@@ -191,7 +204,7 @@ static int build_tables(orc_tables *T, int32_t n, double delta, double lambda, i
     if (n < 1) return ORC_EINVAL;
     if (to_rational(delta, &T->dnum, &T->dden)) return ORC_EINVAL;
     if (to_rational(lambda, &T->lnum, &T->lden)) return ORC_EINVAL;
-    if (lg_override < 0 || (flags & ~ORC_HEURISTIC)) return ORC_EINVAL;
+    if (lg_override < 0 || (flags & ~(ORC_HEURISTIC | ORC_JUMP))) return ORC_EINVAL;
     T->n = n;
     int err = 0;
     /* t: smallest t with (dden+dnum)^t >= n * dden^t */
@@ -346,6 +359,7 @@ typedef struct {
     int64_t st_rounds, st_moves, st_visits, st_dl_evals, st_dl_visits;
     int32_t st_max_level_moves; /* insert: max levels one vertex climbed; delete: max moves of one vertex */
     int32_t st_dir_error;       /* 1 if a vertex moved against the batch's direction */
+    int jump;                   /* ORC_JUMP: insertion violators move to their targets */
     /* orientation tracking (Algorithm 5): the last batch's levels before it, its
        kind and its valid (applied) edges */
     int track;
@@ -489,6 +503,7 @@ orc_plds *orc_create_ex(int32_t n, double delta, double lambda, int32_t lg_overr
     }
     for (int32_t i = 0; i < n; ++i) h->dl[i] = -1;
     h->last_op = -1;
+    h->jump = (flags & ORC_JUMP) != 0;
     return h;
 }
 
@@ -593,6 +608,28 @@ static void reset_stats(orc_plds *h) {
  */
 static int track_batch(orc_plds *h, int op, const uint64_t *keys, int64_t m);
 
+/* Number of neighbours of v on level x or above (by definition). */
+static int32_t count_at_or_above(const orc_plds *h, int32_t v, int32_t x) {
+    int32_t c = 0;
+    for (int32_t j = 0; j < h->deg[v]; ++j) c += h->level[h->nbr[v][j]] >= x;
+    return c;
+}
+
+/* ORC_JUMP: the target of a violator v of level l -- the smallest x > l with
+   count_at_or_above(v, x) <= upmax[gn(x)] on the current levels.  The count does not
+   rise and the bound does not fall as x grows, so the test is false below the answer
+   and true from it on; the top level passes (its bound is n), and bisection finds
+   the first x that passes. */
+static int32_t jump_target(const orc_plds *h, int32_t v, int32_t l) {
+    int32_t lo = l + 1, hi = h->T.K - 1;
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (count_at_or_above(h, v, mid) <= h->T.upmax[gn(h, mid)]) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 int orc_insert(orc_plds *h, const int32_t *edges, int64_t B) {
     reset_stats(h);
     uint64_t *keys = NULL;
@@ -636,6 +673,41 @@ int orc_insert(orc_plds *h, const int32_t *edges, int64_t B) {
         if (movers.len == 0) continue;
         if (l + 1 >= K) { rc = ORC_EINTERNAL; goto done; } /* top group can never be violated */
         h->st_rounds++;
+        if (h->jump) {
+            /* targets on the pre-round levels (the other movers are still on l) */
+            int32_t *tgt = (int32_t *)malloc(sizeof(int32_t) * movers.len);
+            if (!tgt) { rc = ORC_ENOMEM; goto done; }
+            for (int32_t i = 0; i < movers.len; ++i) tgt[i] = jump_target(h, movers.a[i], l);
+            for (int32_t i = 0; i < movers.len; ++i) {
+                int32_t v = movers.a[i];
+                h->level[v] = tgt[i];
+                h->marked[v] = 1;
+                h->st_moves++;
+                h->st_visits += h->deg[v];
+            }
+            /* a neighbour above l may have gained an up-neighbour: test it on its level */
+            int32_t sj = next_stamp(h);
+            for (int32_t i = 0; i < movers.len; ++i) {
+                int32_t v = movers.a[i];
+                for (int32_t j = 0; j < h->deg[v]; ++j) {
+                    int32_t w = h->nbr[v][j], lw = h->level[w];
+                    if (lw <= l || h->stamp[w] == sj) continue;
+                    h->stamp[w] = sj;
+                    if (up_of(h, w) > h->T.upmax[gn(h, lw)]) {
+                        h->marked[w] = 1;
+                        if (iv_push(&bucket[lw], w)) { free(tgt); rc = ORC_ENOMEM; goto done; }
+                    }
+                }
+            }
+            /* movers stay candidates on their new level while they violate there */
+            for (int32_t i = 0; i < movers.len; ++i) {
+                int32_t v = movers.a[i];
+                if (up_of(h, v) <= h->T.upmax[gn(h, tgt[i])]) h->marked[v] = 0;
+                if (iv_push(&bucket[tgt[i]], v)) { free(tgt); rc = ORC_ENOMEM; goto done; }
+            }
+            free(tgt);
+            continue;
+        }
         /* mark and move every violator to level l+1 */
         for (int32_t i = 0; i < movers.len; ++i) {
             int32_t v = movers.a[i];

@@ -50,6 +50,10 @@ MUTANTS = {
     "static_estimate": ("est[v] = thr[bkt];", "est[v] = bkt > 0 ? thr[bkt - 1] : 0.5;"),
     # static k-core: the next bucket taken at the same threshold without the (2+eps) test
     "static_no_threshold_test": ("if (thr[next] <= (2.0 + eps) * thr[t]) bkt = next;", "if (1) bkt = next;"),
+    # jump mode: the target taken one level past the first level that passes
+    "jump_overshoot": ("    return lo;\n}\n\nint orc_insert(", "    return lo + 1;\n}\n\nint orc_insert("),
+    # jump mode: the other movers counted on their level l as if they were above it
+    "jump_counts_comovers": ("c += h->level[h->nbr[v][j]] >= x;", "c += h->level[h->nbr[v][j]] >= x - 1;"),
     # levels per group 4t replaced by t
     "group_size": ("T->Lg = lg_override > 0 ? lg_override : 4 * (t > 1 ? t : 1);",
                    "T->Lg = lg_override > 0 ? lg_override : (t > 1 ? t : 1);"),

@@ -214,29 +214,62 @@ def test_deletion_worked_example():
 @pytest.mark.parametrize("delta,lam,lpg", [(0.4, 3.0, 0), (0.4, 3.0, 3), (1.0, 3.0, 3),
                                            (0.2, 1.0, 2), (1.6, 12.0, 0)])
 def test_rules_match_global_fixpoint(delta, lam, lpg):
+    """Both insertion procedures -- one level a round (Algorithm 2) and the jump mode
+    (violators straight to their targets) -- land on the global fixpoint's levels;
+    the jump mode never makes more moves (each of its moves climbs at least one level
+    of the same total climb)."""
     rng = np.random.default_rng(int(delta * 100 + lam + lpg))
     for trial in range(12):
         n = int(rng.integers(4, 26))
         allp = _ref.all_pairs(n)
         h = O.OraclePLDS(n, delta, lam, lpg)
+        hj = O.OraclePLDS(n, delta, lam, lpg, flags=O.JUMP)
         g = _ref.GlobalPLDS(n, delta, lam, lpg)
         present = set()
         for step in range(10):
             if rng.random() < 0.6 or not present:
                 k = int(rng.integers(1, max(2, len(allp) // 3)))
                 pick = [allp[i] for i in rng.choice(len(allp), size=k, replace=False)]
-                assert h.insert(pick) == 0
+                assert h.insert(pick) == 0 and hj.insert(pick) == 0
+                assert hj.stats()["moves"] <= h.stats()["moves"]
                 g.insert(pick)
                 present |= set(pick)
             else:
                 pl = sorted(present)
                 k = int(rng.integers(1, len(pl) + 1))
                 pick = [pl[i] for i in rng.choice(len(pl), size=k, replace=False)]
-                assert h.delete(pick) == 0
+                assert h.delete(pick) == 0 and hj.delete(pick) == 0
                 g.delete(pick)
                 present -= set(pick)
             assert list(h.levels()) == g.level, (trial, step)
-            assert h.check() == 0
+            assert list(hj.levels()) == g.level, (trial, step)
+            assert h.check() == 0 and hj.check() == 0
+
+
+def test_jump_mode_hand_example():
+    """n = 12, delta = 0.4, lambda = 3: t = 8 (1.4^7 < 12 <= 1.4^8), 32 levels a group,
+    UPMAX = floor(3 * 1.4^i) = 3, 4, 5, 8, 11, 12, ... and DNMIN = ceil(1.4^i) = 1, 2, 2,
+    3, 4, 6, ...  A clique on vertices 1..11 sits on level 160 (group 5: up 10 <= 12,
+    up* 10 >= DNMIN[4] = 4).  Inserting (0, 1..9) leaves vertex 0 on level 0 with up 9
+    > 3.  Its target is the first level whose group allows 9 up-neighbours, group 4
+    (UPMAX 11) from level 128 on, below the clique: Algorithm 2 climbs there in 128
+    rounds of one move, the jump mode in one."""
+    T = O.tables(12)
+    assert T["t"] == 8 and T["Lg"] == 32
+    assert list(T["upmax"][:6]) == [3, 4, 5, 8, 11, 12] and list(T["dnmin"][:6]) == [1, 2, 2, 3, 4, 6]
+    clique = [(u, v) for u in range(1, 12) for v in range(u + 1, 12)]
+    for flags, rounds in ((0, 128), (O.JUMP, 1)):
+        h = O.OraclePLDS(12, flags=flags)
+        h.add_edges_raw(clique)
+        for v in range(1, 12):
+            h.set_level(v, 160)
+        assert h.check() == 0
+        assert h.insert([(0, v) for v in range(1, 10)]) == 0
+        lv = h.levels()
+        assert lv[0] == 128 and all(lv[1:] == 160)
+        s = h.stats()
+        assert s["rounds"] == rounds and s["moves"] == rounds and s["max_vertex_moves"] == 128
+        assert h.check() == 0
 
 
 # ----------------------------------------------------------------------------
