@@ -729,6 +729,8 @@ struct RoundStage {
     int32_t *tmp;
     int4 *ph4;
     int32_t *phs;
+    int32_t *ff;             // block's climbing movers: {count, smallest new up-degree, lowest other level}
+    unsigned long long *ff64;  // their {degree sum, new up-degree sum}
 };
 
 // Shared ints of a staging area whose capacities are the defaults >> shift
@@ -759,12 +761,17 @@ __device__ __forceinline__ RoundStage stage_setup(int32_t *base, int shift) {
     st.movers = hdr + 8;
     st.bmin = hdr + 9;
     st.tmp = hdr + 10;  // 4 ints
+    st.ff = hdr + 14;   // 3 ints
+    st.ff64 = reinterpret_cast<unsigned long long *>(hdr + 18);  // 2 x 64 bit
     if (threadIdx.x == 0) {
         hdr[0] = 0; hdr[1] = cf;
         hdr[2] = 0; hdr[3] = ct;
         hdr[4] = 0; hdr[5] = cc;
         hdr[6] = 0; hdr[7] = cp;
         hdr[8] = 0; hdr[9] = kInf;
+        hdr[14] = 0; hdr[15] = kInf; hdr[16] = kInf;
+        st.ff64[0] = 0;
+        st.ff64[1] = 0;
     }
     __syncthreads();
     return st;
@@ -993,22 +1000,39 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
 // to the next initial-candidate level, tested in a phase of its own.  Every flag
 // is cleared at the end.  The result is the same as rounds evaluated one level
 // after another (the same-sequence lemma): the marks depend only on final counts.
+//
+// Pure rounds are skipped.  When round x ends with exactly its movers M climbing
+// on (none stopped, nobody new marked), a following round y moves M from y to y+1
+// and changes nothing else as long as no neighbour of M outside M sits on levels
+// y .. y+2 (nobody left behind, nobody gaining an up- or up*-neighbour), no initial
+// candidate sits on y+1 and every member still violates on y+1 (its up-degree is
+// unchanged, so this holds while the cutoff stays below M's smallest up-degree).
+// The scan of round x finds the lowest level >= x+1 of a non-mover neighbour and
+// the climbing movers' smallest up-degree, so the team can run the next j pure
+// rounds at once: the level jumps by j, and rounds, moves and visits are counted
+// as the j rounds would have counted them.  The members' level words still read
+// x+1 (with their flag) until their next scan rewrites them; readers of that scan
+// take a flagged word anywhere from x+1 up as a mover (lmo = x+1), and j is even so
+// that the flag's parity is the one of the new level.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int32_t level_flag(int32_t l) { return (l & 1) ? kFlagOdd : kFlagEven; }
 
 // Effects of a mover of level l on its neighbour w (level word raw).  Returns bit 0
 // if w became a mover of level l + 1 here, bit 1 if w stays on level l + 1 or above
-// after the round (an entry of the mover's up-list for its next move).
-__device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t fcur,
-                                          int32_t fnext, int32_t cut_next, int &cnt_l) {
+// after the round (an entry of the mover's up-list for its next move).  Movers of
+// l read as flagged words on levels lmo .. l + 1 (lmo = l unless pure rounds were
+// just skipped); low gets the lowest level above l of a neighbour that is no mover.
+__device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t lmo,
+                                          int32_t fcur, int32_t fnext, int32_t cut_next, int &cnt_l, int32_t &low) {
     if (!valid_id(g, w)) return 0;  // empty slot or tombstone
     const int32_t f = raw & kLevelMask;
-    if ((raw & fcur) && (f == l || f == l + 1)) return 2;  // a mover of level l as well
+    if ((raw & fcur) && f >= lmo && f <= l + 1) return 2;  // a mover of level l as well
     if (f == l) {
         cnt_l++;
         return 0;
     }
     if (f < l) return 0;
+    low = min(low, f);
     if (f == l + 1) {
         if (atomicAdd(&g.up[w], 1) == cut_next) return 2 | (!(atomicOr(&g.level[w], fnext) & fnext) ? 1 : 0);
     } else if (f == l + 2) {
@@ -1030,6 +1054,15 @@ __device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, i
     const bool again = nu > cut_next;
     g.level[v] = (l + 1) | fcur | (again ? fnext : 0);
     return again;
+}
+
+// A mover that climbs on: its new up-degree and degree go into the block's totals
+// (shared atomics; published once per block at the end of the phase).
+__device__ __forceinline__ void ff_note(const RoundStage &st, int32_t nu, int32_t deg) {
+    atomicAdd(&st.ff[0], 1);
+    atomicMin(&st.ff[1], nu);
+    atomicAdd(&st.ff64[0], (unsigned long long)deg);
+    atomicAdd(&st.ff64[1], (unsigned long long)nu);
 }
 
 // Queue the table scans of the lanes' newly marked vertices (their first move of
@@ -1116,6 +1149,8 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
     int mc = 0;
     int spos = 0;
     int32_t l = nlev > 0 ? g.levlist[spos++] : 0;
+    int32_t lmo = l;     // movers of l read as flagged words on levels lmo .. l + 1
+    bool ffed = false;   // pure rounds were skipped just before this phase
     bool scan = false;  // this phase scans the movers of l (else it tests the initial candidates on l)
     for (int k = 0; nlev > 0; ++k) {
         if ((scan && l >= g.K - 1) || k > 2 * g.K + 4) {  // the top group is never violated
@@ -1136,7 +1171,13 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             g.ctl->icl[old] = 0;
             g.ctl->imcnt[old] = 0;
             g.ctl->ltop[old] = 0;  // allocated from in phase k + 1 (its contents are read now)
+            g.ctl->icont[old] = 0;
+            g.ctl->iminup_c[old] = 0;
+            g.ctl->ilow_c[old] = 0;
+            g.ctl->isdeg[old] = 0;
+            g.ctl->isup[old] = 0;
         }
+        int32_t low = kInf;  // lowest level above l of a neighbour of a mover that is no mover
         st.tl.gcnt = &g.ctl->itl[nxt];
         st.tl.glist = g.TL[nxt];
         st.tl.gcap = g.n;
@@ -1156,6 +1197,10 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 has_init = st.phs[4] == l + 1;
                 s_lo = st.phs[5];
                 s_hi = st.phs[6];
+                if (ffed && has_init) {  // fetched for the level before the skip
+                    s_lo = g.bins[l];
+                    s_hi = g.bins[l + 1];
+                }
             } else {
                 m = g.ctl->imcnt[cur];
                 tlc = g.ctl->itl[cur];
@@ -1180,7 +1225,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 const int ng = have ? (1 << it.y) >> 2 : 0;
                 const int32_t up_v = have ? g.up[it.x] : 0;  // issued with the slot loads
                 const int maxg = (int)__reduce_max_sync(kFull, (unsigned)ng);
-                int cnt_l = 0;
+                int cnt_l = 0, ideg = 0;
                 for (int j0 = 0; j0 < maxg; j0 += 4) {
                     int32_t ws[16], lv[16];
 #pragma unroll
@@ -1193,14 +1238,16 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     unsigned push = 0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        visits += ws[q] >= 0;
-                        if (ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cnt_l) & 1) push |= 1u << q;
+                        ideg += ws[q] >= 0;
+                        if (ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cnt_l, low) & 1) push |= 1u << q;
                     }
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
                     marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
                 }
+                visits += ideg;
                 upv += up_v;
                 const bool again = have && ins_finish_mover(g, it.x, up_v, cnt_l, l, fcur, fnext, cut_next);
+                if (again) ff_note(st, up_v - cnt_l, ideg);
                 enqueue_ins(g, st, again, it.x, have ? 1 << it.y : 0, (int64_t)it.z * 4, -1, 0, 0, k + 1, wsm);
             }
             // chunk items: four per warp iteration, all loads of a step issued together;
@@ -1238,7 +1285,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 unsigned push = 0, keep = 0;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int r = ins_effect(g, ws[q], lv[q], l, fcur, fnext, cut_next, cl4[q >> 2]);
+                    const int r = ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cl4[q >> 2], low);
                     if (r & 1) push |= 1u << q;
                     if (r & 2) keep |= 1u << q;
                 }
@@ -1306,6 +1353,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     nul = upl - total;
                     cont = ins_finish_mover(g, mine.x, upl, total, l, fcur, fnext, cut_next);
                     for (int p = nul; cont && lol >= 0 && (p & 3); ++p) lwr[(int64_t)lol * 4 + p] = kEmpty;
+                    if (cont) ff_note(st, nul, dgl);
                 }
                 // a mover that keeps climbing is scanned next from its up-list, or from
                 // its table again when its list did not fit
@@ -1323,12 +1371,30 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 enqueue_ins(g, st, cont, mine.x, mc_cap, moff, (cont && lol >= 0) ? nul : -1, lol, nul, k + 1, wsm);
             }
             marks_flush(g, st, mbuf, mc, k + 1, wsm);
+            low = (int32_t)__reduce_min_sync(kFull, (unsigned)low);
+            if (lane == 0 && low < kInf) atomicMin(&st.ff[2], low);
         }
         const uint64_t t_work = (g.trace && T.leader()) ? global_ns() : 0;
         stage_flush_round(g, st, 6u);
-        if (threadIdx.x == 0 && *st.movers) {
-            atomicAdd(&g.ctl->imcnt[nxt], *st.movers);
-            *st.movers = 0;
+        if (threadIdx.x == 0) {
+            if (*st.movers) {
+                atomicAdd(&g.ctl->imcnt[nxt], *st.movers);
+                *st.movers = 0;
+            }
+            if (st.ff[0]) {  // the block's climbing movers (complements: zero means none)
+                atomicAdd(&g.ctl->icont[nxt], st.ff[0]);
+                atomicMax(&g.ctl->iminup_c[nxt], kInf - st.ff[1]);
+                atomicAdd(&g.ctl->isdeg[nxt], st.ff64[0]);
+                atomicAdd(&g.ctl->isup[nxt], st.ff64[1]);
+                st.ff[0] = 0;
+                st.ff[1] = kInf;
+                st.ff64[0] = 0;
+                st.ff64[1] = 0;
+            }
+            if (st.ff[2] < kInf) {
+                atomicMax(&g.ctl->ilow_c[nxt], kInf - st.ff[2]);
+                st.ff[2] = kInf;
+            }
         }
         // the level the next phase scans if it has movers, and its initial-candidate
         // entry; warp 0 fetches them with the next phase's counts and each warp's
@@ -1359,6 +1425,12 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                         st.phs[5] = l2 < g.K ? g.bins[l2] : 0;
                     } else if (ln == 21) {
                         st.phs[6] = l2 < g.K ? g.bins[l2 + 1] : 0;
+                    } else if (ln == 22) {
+                        st.phs[7] = g.ctl->icont[nxt];
+                    } else if (ln == 23) {
+                        st.phs[8] = g.ctl->ilow_c[nxt];
+                    } else if (ln == 24) {
+                        st.phs[9] = g.ctl->iminup_c[nxt];
                     }
                 },
                 st.phs);
@@ -1366,18 +1438,53 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             passed = T.sync();
         }
         if (!passed) return false;
-        if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
-            int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
-            const uint64_t t_end = global_ns();
-            rec[0] = l; rec[1] = scan ? 1 : 0; rec[2] = m; rec[3] = tlc; rec[4] = clc;
-            rec[5] = (int32_t)(t_work - t_phase); rec[6] = (int32_t)(t_end - t_work);
-            rec[7] = rec[8] = rec[9] = rec[10] = rec[11] = 0;
-        }
         // the next phase: the movers of l + 1 (after a scan) or of l (after a test),
         // else the initial candidates of the next level that has some
         spos = spos2;
         l = l2;
-        if (Team::kGrid ? st.phs[1] > 0 : g.ctl->imcnt[nxt] > 0) {
+        lmo = l;
+        ffed = false;
+        const int32_t nm = Team::kGrid ? st.phs[1] : g.ctl->imcnt[nxt];
+        int32_t skip = 0;
+        if (scan && m > 0 && nm == m) {
+            const int32_t ncont = Team::kGrid ? st.phs[7] : g.ctl->icont[nxt];
+            if (ncont == m) {  // the same movers climb on to l: skip the pure rounds ahead
+                const int32_t lowc = Team::kGrid ? st.phs[8] : g.ctl->ilow_c[nxt];
+                const int32_t mupc = Team::kGrid ? st.phs[9] : g.ctl->iminup_c[nxt];
+                const int64_t low_lvl = lowc ? (int64_t)(kInf - lowc) : (int64_t)kInf;
+                const int32_t minup = kInf - mupc;
+                const int64_t init_lvl = spos < nlev ? (int64_t)(Team::kGrid ? st.phs[4] : g.levlist[spos]) : (int64_t)kInf;
+                int gg = l / g.Lg;  // highest group whose cutoff stays below the smallest up-degree
+                while (gg + 1 < g.G && sh_upmax[gg + 1] < minup) ++gg;
+                const int64_t top = (int64_t)(gg + 1) * g.Lg - 1;
+                // round l - 1 just ran; rounds l .. l + j - 1 are pure while no other
+                // neighbour sits on l .. l + j + 1, no initial candidate on l + 1 .. l + j
+                // and every member still violates on l + j
+                int64_t j = min(min(low_lvl - l - 2, init_lvl - l - 1), top - l);
+                j &= ~(int64_t)1;  // even: the movers' flag keeps its parity
+                if (j >= 2) {
+                    skip = (int32_t)j;
+                    if (T.leader()) {
+                        atomicAdd(&g.ctl->st[kStRounds], (unsigned long long)j);
+                        atomicAdd(&g.ctl->st[kStMoves], (unsigned long long)j * (unsigned long long)m);
+                        atomicAdd(&g.ctl->st[kStVisits], (unsigned long long)j * g.ctl->isdeg[nxt]);
+                        atomicAdd(&g.ctl->st[kStUpVisits], (unsigned long long)j * g.ctl->isup[nxt]);
+                    }
+                    lmo = l;
+                    l += skip;
+                    ffed = true;
+                }
+            }
+        }
+        if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
+            int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
+            const uint64_t t_end = global_ns();
+            rec[0] = scan ? l2 - 1 : l2; rec[1] = scan ? 1 : 0; rec[2] = m; rec[3] = tlc; rec[4] = clc;
+            rec[5] = (int32_t)(t_work - t_phase); rec[6] = (int32_t)(t_end - t_work);
+            rec[7] = skip;
+            rec[8] = rec[9] = rec[10] = rec[11] = 0;
+        }
+        if (nm > 0) {
             scan = true;
             continue;
         }

@@ -47,6 +47,15 @@ struct Ctl {
     int32_t imcnt[3];     // insertion: movers marked for a phase (phase index mod 3)
     int32_t itl[3];       // insertion: thread-mode scan items of a phase
     int32_t icl[3];       // insertion: chunk scan items of a phase
+    // insertion, per phase (index mod 3), about the movers of level l that climb on
+    // to l + 1: how many; kInf minus their smallest new up-degree; their degree and
+    // new up-degree sums; kInf minus the lowest level >= l + 1 of a neighbour of a
+    // mover of l that is not itself a mover (complements, so that zero means none)
+    int32_t icont[3];
+    int32_t iminup_c[3];
+    int32_t ilow_c[3];
+    unsigned long long isdeg[3];
+    unsigned long long isup[3];
     int32_t mcnt[2];      // table growth / deletion movers
     int32_t tlcnt[2];     // thread-mode movers
     int32_t clcnt[2];     // chunk items
