@@ -112,12 +112,21 @@ plds_t *plds_create(int32_t n, double delta, double lambda);
 /*
  * As plds_create, plus: levels_per_group (0 = the paper's 4*ceil(log_{1+delta} n);
  * a positive value overrides it), allocator (NULL = cudaMallocAsync/cudaFreeAsync),
- * stream (a cudaStream_t; NULL = the legacy default stream), flags (0, or
+ * stream (a cudaStream_t; NULL = the legacy default stream), flags (0, or a sum of:
  * PLDS_FLAG_HEURISTIC: Invariant 1's coefficient 2 + 3/lambda replaced by 1.1, the
  * experiments section's "heuristic parameters" -- both invariants still hold, the
- * efficiency and approximation bounds do not; other bits: PLDS_EINVAL).
+ * efficiency and approximation bounds do not;
+ * PLDS_FLAG_JUMP: insertion batches take the Experiments section's implementation
+ * variant ("filter and sort" desire-levels for the vertices moved up, read as: each
+ * round, every violator of Invariant 1 on the lowest level l that holds one moves at
+ * once to the lowest level above l on which it satisfies Invariant 1 with every
+ * other vertex where it is) instead of Algorithm 2's one level per round -- the
+ * levels after every batch are Algorithm 2's, the rounds and moves statistics are
+ * the variant's; deletions are unchanged;
+ * other bits: PLDS_EINVAL).
  */
 #define PLDS_FLAG_HEURISTIC 1u
+#define PLDS_FLAG_JUMP 2u
 plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
                        const plds_allocator *allocator, void *stream, uint32_t flags);
 

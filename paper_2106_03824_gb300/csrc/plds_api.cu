@@ -133,6 +133,7 @@ struct plds {
     bool custom_alloc = false;
     bool poisoned = false;
     int32_t n = 0;
+    bool jump = false;  // insertion: the jump variant (PLDS_FLAG_JUMP)
     Tables T;
     plds_tuning tune{};
     int64_t wait_limit_ns = 20ll * 1000 * 1000 * 1000;
@@ -372,6 +373,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
     g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 1024;
     g.list_cap = h->tune.list_cap > 0 ? h->tune.list_cap : 256;
+    g.jump = h->jump ? 1 : 0;
     g.wait_limit_ns = h->wait_limit_ns;
     g.test_delay_us = h->tune.test_delay_us;
     g.barrier_sleep_ns = h->tune.barrier_sleep_ns == 0 ? 32 : (h->tune.barrier_sleep_ns < 0 ? 0 : h->tune.barrier_sleep_ns);
@@ -545,7 +547,8 @@ extern "C" {
 
 plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_per_group,
                        const plds_allocator *allocator, void *stream, uint32_t flags) {
-    if ((flags & ~(uint32_t)PLDS_FLAG_HEURISTIC) != 0 || (allocator && (!allocator->alloc || !allocator->free))) {
+    if ((flags & ~(uint32_t)(PLDS_FLAG_HEURISTIC | PLDS_FLAG_JUMP)) != 0 ||
+        (allocator && (!allocator->alloc || !allocator->free))) {
         set_status(PLDS_EINVAL);
         return nullptr;
     }
@@ -573,6 +576,7 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
         h->custom_alloc = true;
     }
     h->n = n;
+    h->jump = (flags & PLDS_FLAG_JUMP) != 0;
     const size_t N = (size_t)n;
     const size_t G = (size_t)h->T.G, K = (size_t)h->T.K;
     h->pool_cap = std::max<int64_t>(1 << 20, 8 * (int64_t)n);

@@ -2011,6 +2011,298 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
 }
 
 // ---------------------------------------------------------------------------
+// Insertion, jump variant (the implementation note of the Experiments section:
+// a filter and sort computes a desire-level for the vertices moved up instead of
+// moving them one level at a time).  Read as: each round takes the lowest level l
+// that holds a violator of Invariant 1; every violator on l moves at once to its
+// target, the lowest level above l on which it would satisfy Invariant 1 with
+// every other vertex where it is (the other movers still on l).  Final levels
+// equal Algorithm 2's (both reach the least assignment at or above the starting
+// levels under which Invariant 1 holds everywhere); rounds and moves differ.
+//
+// Violators wait in a pending list {v, level} (each vertex at most once: a vertex
+// is listed when it starts to violate and stays a violator until its round).
+// Round r, two team barriers:
+//   A: the previous round's movers lose their flag; the pending entries on l
+//      become this round's movers (flag of r's parity in the level word, listed in
+//      TL[r mod 3]), the others carry over; the warp that takes a mover computes
+//      its target from a histogram of its neighbours' levels above l (levels read
+//      before any move of the round: the flags are masked), a block does it for a
+//      large table; targets go to dlv.
+//   B: every mover scans its table once more: a neighbour that is a mover counts
+//      at its target, any other at its level; a non-mover w on level lw gains an
+//      up-neighbour if l < lw <= t and an up*-neighbour if l + 1 < lw <= t + 1, and
+//      joins the pending list when that first takes its up-degree past its cutoff;
+//      the mover's up and up* are recounted and it stays pending on t if it still
+//      violates there.  The flag stays on until the next round's phase A, so every
+//      reader of B tells movers from the rest.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t round_flag(int r) { return (r & 1) ? kFlagOdd : kFlagEven; }
+
+// Smallest x in [lo, hi] (hi - lo < 256) with above + sum_{y=x..hi} h[y-lo] <= upmax
+// of x's group, or -1.  The count falls and the bound rises with x, so the test
+// fails below the answer and passes from it on.  One warp.
+__device__ __forceinline__ int warp_jump_find(const int32_t *h, int lo, int hi, int above, int32_t Lg,
+                                              const int32_t *sh_upmax) {
+    const int lane = lane_id();
+    int local = 0;  // lane L covers offsets 8L .. 8L+7, ascending
+    for (int b = 0; b < 8; ++b)
+        if (lo + 8 * lane + b <= hi) local += h[8 * lane + b];
+    int incl = local;  // suffix over the lanes above
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_down_sync(kFull, incl, o);
+        if (lane + o < 32) incl += y;
+    }
+    int run = above + incl - local;
+    int found = -1;
+    for (int b = 7; b >= 0; --b) {
+        const int x = lo + 8 * lane + b;
+        if (x <= hi) {
+            run += h[8 * lane + b];  // run = neighbours on x or above
+            if (run <= sh_upmax[x / Lg]) found = x;
+        }
+    }
+    const unsigned m = __ballot_sync(kFull, found >= 0);
+    return m ? __shfl_sync(kFull, found, __ffs(m) - 1) : -1;
+}
+
+// Target of a mover v of level l (warp, or whole block when blk): windows of 256
+// levels from l + 1 up, one table scan each (the first almost always holds it).
+template <bool blk>
+__device__ int32_t jump_target(const GraphCtx &g, int32_t v, int32_t l, const int32_t *sh_upmax, int32_t *hist,
+                               int32_t *res) {
+    const int32_t ng = g.cap[v] >> 2;
+    const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[v]);
+    const int start = blk ? (int)threadIdx.x : lane_id();
+    const int stride = blk ? (int)blockDim.x : 32;
+    for (int32_t lo = l + 1; lo < g.K; lo += kWindow) {
+        const int32_t hi = min(lo + kWindow - 1, g.K - 1);
+        for (int k = start; k <= kWindow; k += stride) hist[k] = 0;
+        if (blk) __syncthreads(); else __syncwarp();
+        scan_levels(g, t4, ng, start, stride, [&](int32_t raw) {
+            const int32_t x = raw & kLevelMask;
+            if (x > hi) atomicAdd(&hist[kWindow], 1);
+            else if (x >= lo) atomicAdd(&hist[x - lo], 1);
+        });
+        if (blk) __syncthreads(); else __syncwarp();
+        int found;
+        if (blk) {
+            if (threadIdx.x < 32) {
+                const int f = warp_jump_find(hist, lo, hi, hist[kWindow], g.Lg, sh_upmax);
+                if (threadIdx.x == 0) *res = f;
+            }
+            __syncthreads();
+            found = *res;
+            __syncthreads();
+        } else {
+            found = warp_jump_find(hist, lo, hi, hist[kWindow], g.Lg, sh_upmax);
+            __syncwarp();
+        }
+        if (found >= 0) return found;
+    }
+    return g.K - 1;  // not reached: the top group's bound is n
+}
+
+// Append the lanes' {v, level} with pred to pending list p (warp-collective).
+__device__ __forceinline__ void jump_push(const GraphCtx &g, int p, bool pred, int32_t v, int32_t lv) {
+    const int pos = warp_append(&g.ctl->jpend[p], pred);
+    if (pred) {
+        if (pos < 2 * g.n) g.P[p][pos] = make_int4(v, lv, 0, 0);
+        else report(g, kErrListOverflow, 20, pos, v, lv);
+    }
+    const int32_t mn = (int32_t)__reduce_min_sync(kFull, pred ? (unsigned)lv : (unsigned)kInf);
+    if (lane_id() == 0 && mn < kInf) atomicMax(&g.ctl->jnext_c[p], kInf - mn);
+}
+
+// Phase B for one mover v (old level l, target tv, round flag flr): warp, or
+// block when blk.  Returns its degree (visits); red: 2 ints of block scratch.
+template <bool blk>
+__device__ int32_t jump_apply(const GraphCtx &g, int32_t v, int32_t l, int32_t tv, int32_t flr, int p,
+                              const int32_t *sh_upmax, int32_t *red) {
+    const int32_t ng = g.cap[v] >> 2;
+    const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[v]);
+    const int start = blk ? (int)threadIdx.x : lane_id();
+    const int stride = blk ? (int)blockDim.x : 32;
+    int cu = 0, cs = 0, dg = 0;
+    const int ng_iter = blk ? ((ng + stride - 1) / stride) * stride : ((ng + 31) & ~31);
+    for (int j = start; j < ng_iter; j += stride) {  // every lane of a warp runs every step
+        const int4 q = j < ng ? t4[j] : empty4();
+        const int32_t ws[4] = {q.x, q.y, q.z, q.w};
+        int32_t raw[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) raw[u] = valid_id(g, ws[u]) ? g.level[ws[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bool push = false;
+            int32_t lw = 0;
+            if (raw[u] >= 0) {
+                ++dg;
+                int32_t fw;
+                if (raw[u] & flr) {
+                    fw = g.dlv[ws[u]];  // a mover: counts at its target
+                } else {
+                    lw = raw[u] & kLevelMask;
+                    fw = lw;
+                    if (l < lw && lw <= tv) push = atomicAdd(&g.up[ws[u]], 1) == sh_upmax[lw / g.Lg];
+                    if (l + 1 < lw && lw <= tv + 1) atomicAdd(&g.upstar[ws[u]], 1);
+                }
+                cu += fw >= tv;
+                cs += fw >= tv - 1;
+            }
+            if (__any_sync(kFull, push)) jump_push(g, p, push, ws[u], lw);
+        }
+    }
+    cu = warp_sum(cu);
+    cs = warp_sum(cs);
+    dg = warp_sum(dg);
+    if (blk) {
+        if (threadIdx.x == 0) red[0] = red[1] = red[2] = 0;
+        __syncthreads();
+        if (lane_id() == 0) {
+            atomicAdd(&red[0], cu);
+            atomicAdd(&red[1], cs);
+            atomicAdd(&red[2], dg);
+        }
+        __syncthreads();
+        cu = red[0];
+        cs = red[1];
+        dg = red[2];
+        __syncthreads();
+    }
+    const bool lead = blk ? threadIdx.x < 32 : true;  // one warp finishes the mover
+    if (lead) {
+        if (lane_id() == 0) {
+            g.up[v] = cu;
+            g.upstar[v] = cs;
+            g.level[v] = tv | flr;  // still flagged: readers of this phase take dlv
+        }
+        jump_push(g, p, lane_id() == 0 && cu > sh_upmax[tv / g.Lg], v, tv);
+    }
+    return dg;
+}
+
+template <class Team>
+__device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *whist,
+                                int32_t *sh_block) {
+    const int lane = lane_id();
+    const int32_t tc = g.ctl->tcount;
+    // every endpoint of the batch that violates now is pending on its level
+    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
+        const int i = i0 + lane;
+        bool v_ = false;
+        int32_t x = 0, lx = 0;
+        if (i < tc) {
+            x = g.touched[i];
+            g.inc[x] = 0;
+            lx = g.level[x];
+            v_ = g.up[x] > sh_upmax[lx / g.Lg];
+        }
+        jump_push(g, 0, v_, x, lx);
+    }
+    if (!T.sync()) return false;
+    unsigned long long visits = 0;
+    int r = 0;
+    for (;; ++r) {
+        const int cur = r & 1, nxt = cur ^ 1;
+        const int32_t nc = g.ctl->jnext_c[cur];
+        if (nc == 0) break;
+        const int32_t l = kInf - nc;
+        if (l >= g.K - 1 || r > g.K + 4) {  // the top group is never violated
+            if (T.leader()) report(g, kErrInternal, 21, l, r, 0);
+            return false;
+        }
+        const int32_t flr = round_flag(r), flp = round_flag(r + 1);
+        const int mi = r % 3, mprev = (r + 2) % 3;
+        // phase A
+        if (T.leader()) {
+            g.ctl->jmov[(r + 1) % 3] = 0;  // last read in phase B of round r - 1
+            g.ctl->jbig[nxt] = 0;
+        }
+        if (r > 0) {
+            const int32_t pm = g.ctl->jmov[mprev];
+            for (int i = T.tid(); i < pm; i += T.nthreads()) atomicAnd(&g.level[g.TL[mprev][i].x], ~flp);
+        }
+        const int32_t pc = g.ctl->jpend[cur];
+        for (int i0 = T.wid() * 32; i0 < pc; i0 += T.nwarps() * 32) {
+            const int i = i0 + lane;
+            const int4 e = i < pc ? g.P[cur][i] : make_int4(0, kInf, 0, 0);
+            const bool mv = i < pc && e.y == l;
+            const bool carry = i < pc && e.y != l;
+            int32_t c = 0;
+            if (mv) {
+                if ((g.level[e.x] & kLevelMask) != l) report(g, kErrInternal, 22, e.x, g.level[e.x], l);
+                atomicOr(&g.level[e.x], flr);
+                c = g.cap[e.x];
+            }
+            const bool big = mv && c > g.block_cap;
+            const int pos = warp_append(&g.ctl->jmov[mi], mv);
+            if (mv) g.TL[mi][pos] = make_int4(e.x, c, 0, 0);
+            const int pb = warp_append(&g.ctl->jbig[cur], big);
+            if (big) g.M[0][pb] = make_int4(e.x, c, 0, 0);
+            jump_push(g, nxt, carry, e.x, e.y);
+            unsigned sm = __ballot_sync(kFull, mv && !big);
+            while (sm) {  // the warp computes the targets of its small movers
+                const int src = __ffs(sm) - 1;
+                sm &= sm - 1;
+                const int32_t v = __shfl_sync(kFull, e.x, src);
+                const int32_t t = jump_target<false>(g, v, l, sh_upmax, whist, nullptr);
+                if (lane == 0) g.dlv[v] = t;
+            }
+        }
+        if (!T.sync()) return false;
+        // big tables: a block each (their targets are needed before phase B)
+        const int32_t nb = g.ctl->jbig[cur];
+        for (int b = T.bid(); b < nb; b += T.nthreads() / blockDim.x) {
+            const int32_t v = g.M[0][b].x;
+            const int32_t t = jump_target<true>(g, v, l, sh_upmax, sh_block, sh_block + kWarpHist);
+            if (threadIdx.x == 0) g.dlv[v] = t;
+        }
+        if (nb > 0 && !T.sync()) return false;
+        // phase B
+        const int32_t mc = g.ctl->jmov[mi];
+        if (T.leader()) {
+            atomicAdd(&g.ctl->st[kStRounds], 1ull);
+            atomicAdd(&g.ctl->st[kStMoves], (unsigned long long)mc);
+            g.ctl->jpend[cur] = 0;  // read in phase A; filled again in round r + 1
+            g.ctl->jnext_c[cur] = 0;
+        }
+        for (int i = T.wid(); i < mc; i += T.nwarps()) {
+            const int4 it = g.TL[mi][i];
+            if (it.y > g.block_cap) continue;
+            const int32_t dg = jump_apply<false>(g, it.x, l, g.dlv[it.x], flr, nxt, sh_upmax, nullptr);
+            if (lane == 0) visits += dg;
+        }
+        for (int b = T.bid(); b < nb; b += T.nthreads() / blockDim.x) {
+            const int32_t v = g.M[0][b].x;
+            const int32_t dg = jump_apply<true>(g, v, l, g.dlv[v], flr, nxt, sh_upmax, sh_block + kWarpHist);
+            if (threadIdx.x == 0) visits += dg;
+        }
+        if (r > 0) {  // the previous round's movers that do not move now: target dropped
+            const int32_t pm = g.ctl->jmov[mprev];
+            for (int i = T.tid(); i < pm; i += T.nthreads()) {
+                const int32_t v = g.TL[mprev][i].x;
+                if (!(g.level[v] & flr)) g.dlv[v] = -1;
+            }
+        }
+        if (!T.sync()) return false;
+    }
+    // the last round's movers lose their flag and their target (dlv back to -1)
+    if (r > 0) {
+        const int mlast = (r - 1) % 3;
+        const int32_t pm = g.ctl->jmov[mlast];
+        for (int i = T.tid(); i < pm; i += T.nthreads()) {
+            const int32_t v = g.TL[mlast][i].x;
+            atomicAnd(&g.level[v], kLevelMask);
+            g.dlv[v] = -1;
+        }
+    }
+    visits = warp_sum64(visits);
+    if (lane == 0 && visits) atomicAdd(&g.ctl->st[kStVisits], visits);
+    if (!T.sync()) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // One whole batch (Algorithm 1, one half): returns early when the team stopped
 // (error word set).  sh: shared memory with the group tables, a block-scan
 // scratch and one histogram per warp (the first also serves block-wide
@@ -2074,12 +2366,13 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
         step_apply_insert(T, g);
         if (!T.sync()) return;
         if (tr) tmark[nmark++] = global_ns();
-        if (!ins_sort_candidates(T, g, sh_scan)) return;
+        if (!g.jump && !ins_sort_candidates(T, g, sh_scan)) return;
         if (tr) {
             tmark[nmark++] = global_ns();
             trace_steps(g, tmark, nmark, -1);
         }
-        ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
+        if (g.jump) ins_rounds_jump(T, g, sh_upmax, whist, sh_block);
+        else ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
     } else {
         if (T.leader()) {
             g.ctl->nextmin[0] = kInf;

@@ -56,6 +56,13 @@ struct Ctl {
     int32_t ilow_c[3];
     unsigned long long isdeg[3];
     unsigned long long isup[3];
+    // insertion, jump variant: pending violators in P[i] (round parity) and kInf
+    // minus their lowest level (0: none); movers of a round (index mod 3, in TL)
+    // and those with large tables (round parity, in M[0])
+    int32_t jpend[2];
+    int32_t jnext_c[2];
+    int32_t jmov[3];
+    int32_t jbig[2];
     int32_t mcnt[2];      // table growth / deletion movers
     int32_t tlcnt[2];     // thread-mode movers
     int32_t clcnt[2];     // chunk items
@@ -81,7 +88,7 @@ struct GraphCtx {
     int32_t barrier_sleep_ns;
     int32_t block_cap;     // tables above this many slots get a whole block (desire-levels, rebuilds)
     int32_t list_cap;      // insertion: chunk-scanned tables from this size on get an up-list
-    int32_t pad2;
+    int32_t jump;          // insertion violators move straight to their targets (jump variant)
     int64_t wait_limit_ns;
     const int32_t *upmax;  // [G]
     const int32_t *dnmin;  // [G]

@@ -19,6 +19,7 @@ LIB_PATH = _PKG / "_lib" / "libplds_gb300.so"
 PLDS_OK, PLDS_EINVAL, PLDS_ENOMEM, PLDS_ETIMEOUT, PLDS_EDEVICE, PLDS_EINTERNAL, PLDS_EPOISONED = \
     0, -1, -2, -3, -4, -5, -6
 FLAG_HEURISTIC = 1  # Invariant 1's coefficient 2 + 3/lambda replaced by 1.1
+FLAG_JUMP = 2  # insertion violators move straight to their targets (the experiments' variant)
 _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEOUT", -4: "EDEVICE", -5: "EINTERNAL",
           -6: "EPOISONED"}
 
@@ -177,7 +178,8 @@ class PLDS:
     """One graph on the current CUDA device; wraps a plds_t handle."""
 
     def __init__(self, n: int, delta: float = 0.4, lam: float = 3.0, levels_per_group: int = 0,
-                 torch_allocator: bool = True, stream=None, _borrowed=None, heuristic: bool = False):
+                 torch_allocator: bool = True, stream=None, _borrowed=None, heuristic: bool = False,
+                 jump: bool = False):
         L = load()
         self.n = int(n)
         self._owned = _borrowed is None
@@ -189,7 +191,7 @@ class PLDS:
             st = stream if stream is not None else (_torch_stream() if torch_allocator else None)
             self._h = L.plds_create_ex(self.n, float(delta), float(lam), int(levels_per_group),
                                        ctypes.byref(self._alloc) if self._alloc else None, st,
-                                       FLAG_HEURISTIC if heuristic else 0)
+                                       (FLAG_HEURISTIC if heuristic else 0) | (FLAG_JUMP if jump else 0))
         if not self._h:
             raise PldsError(L.plds_last_status(), "plds_create_ex")
         p = np.zeros(4, np.int32)
