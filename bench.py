@@ -10,12 +10,19 @@ empty, shuffled, batches of 10^6) then Del (all edges, a second shuffle).
 The graph state (adjacency pool, level and counter arrays, ~1 GB) is larger
 than L2, so no explicit L2 flush is done between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+The same line carries the Ins/Del/Mix protocols (Algorithm 2, PLDSOpt's group
+size, the filter+sort insertion variant) and the two system forms on their own
+workloads: serving (a device-resident request loop) and batched (512 graphs in
+one launch per round), each with its clocks and a CPU baseline of the oracle.
 
-N > 1 (under torchrun) runs N independent replicas (a single graph's level
-rounds do not shard); value = all ranks' updates / max time.
---impl reference times the sequential CPU oracle on the host cores on bounded
-samples of the same stream.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--form plain|serving|batched|large] [--no-forms]
+
+N > 1 (under torchrun) runs N independent replicas of the plain form (a single
+graph's level rounds do not shard); value = all ranks' updates / max time.  With
+--form batched the 512 graphs are split over the ranks by a greedy size balance
+(no data-path collective).  --impl reference times the sequential CPU oracle on
+the host cores on bounded samples of the same stream.
 """
 from __future__ import annotations
 
@@ -23,6 +30,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,11 +48,11 @@ from paper_2106_03824_gb300 import workloads as W  # noqa: E402
 METRIC = "edge updates/s at batch 1e6 (Ins/Del/Mix)"
 UNIT = "updates/s"
 
-# dram bytes / algorithmic bytes of the batch kernel, from the ncu capture
+# dram bytes / executed algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": "b311bada918cc187", "dram_per_algo_byte": 0.2269,
-               "capture": "ncu DRAM counters of every k_batch_grid launch of the R-MAT 20 Ins and Del protocols"}
+NCU_TRAFFIC = {"kernel_sha": None, "dram_per_algo_byte": None,
+               "capture": "ncu DRAM counters of three k_batch_grid launches of the R-MAT 20 step stream"}
 
 
 def kernel_sha() -> str:
@@ -56,7 +64,7 @@ def kernel_sha() -> str:
 
 
 def whole_job(dist, updates: float, seconds: float, device: str):
-    """The whole-job figures of a replicas run: the updates of every rank and the
+    """The whole-job figures of a multi-rank run: the updates of every rank and the
     slowest rank's time (one collective each; the identity without a process
     group).  Returns (total updates, max seconds)."""
     if dist is None:
@@ -69,13 +77,45 @@ def whole_job(dist, updates: float, seconds: float, device: str):
     return float(u.item()), float(t.item())
 
 
-def algo_bytes(s: dict) -> int:
-    """Algorithmic bytes of one batch kernel launch: 8 B per submitted edge; 64 B per
-    applied update (2 probes + 2 slot writes of 4 B, 6 counter read-modify-writes of
-    8 B); 4 B per level change; 8 B (id + level) per neighbour a move must examine --
-    an insertion move its up-neighbours (up_visits), a deletion move all its
-    neighbours (visits); 8 B per neighbour read by a desire-level evaluation."""
-    moved = s["up_visits"] if s.get("up_visits") else s["visits"]
+def shard_graphs(sizes, parts: int):
+    """Greedy size balance of independent graphs over `parts` ranks (or processes):
+    graphs in decreasing size, each to the part with the least total so far (the
+    lowest index on ties).  Returns each part's graph indices, ascending."""
+    load = [0] * parts
+    out = [[] for _ in range(parts)]
+    for i in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        p = min(range(parts), key=lambda q: (load[q], q))
+        out[p].append(i)
+        load[p] += sizes[i]
+    return [sorted(x) for x in out]
+
+
+def algo_bytes(s: dict, kind: str) -> int:
+    """Algorithmic bytes of the work one batch-kernel launch executed: 8 B per
+    submitted edge; 64 B per applied update (2 probes + 2 slot writes of 4 B, 6
+    counter read-modify-writes of 8 B); 4 B per level change; 8 B (id + level) per
+    neighbour a move must examine -- an insertion move its up-neighbours
+    (up_visits), a deletion move all its neighbours (visits); 8 B per neighbour read
+    by a desire-level evaluation.  Rounds the kernel skipped (counted, not run) are
+    left out."""
+    moved = (s["up_visits"] - s["skipped_up_visits"]) if kind == "ins" else (s["visits"] - s["skipped_visits"])
+    return (8 * s["submitted"] + 64 * s["valid"] + 4 * (s["moves"] - s["skipped_moves"]) + 8 * moved
+            + 8 * s["dl_visits"])
+
+
+def algo_bytes_survey(s: dict) -> int:
+    """The same work under the scope table's per-unit figures: per move 4 B (level)
+    + 8 B per neighbour of the mover (its degree) + 8 B per neighbour whose counter
+    the move changed (affected); per desire-level evaluation 8 B per neighbour;
+    per valid update 64 B; per submitted edge 8 B.  Executed rounds only."""
+    return (8 * s["submitted"] + 64 * s["valid"] + 4 * (s["moves"] - s["skipped_moves"])
+            + 8 * (s["visits"] - s["skipped_visits"]) + 8 * s["affected"] + 8 * s["dl_visits"])
+
+
+def algo_bytes_with_skipped(s: dict, kind: str) -> int:
+    """algo_bytes with the skipped rounds counted as Algorithm 2 would run them (the
+    bytes of the method's own level-by-level schedule; not a bandwidth figure)."""
+    moved = s["up_visits"] if kind == "ins" else s["visits"]
     return 8 * s["submitted"] + 64 * s["valid"] + 4 * s["moves"] + 8 * moved + 8 * s["dl_visits"]
 
 
@@ -85,6 +125,21 @@ def measured_peaks():
         d = json.loads(p.read_text())
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def host_cpu() -> dict:
+    """The host CPU's model (lscpu) and its logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "logical_cores": os.cpu_count(),
+            "arch": platform.machine()}
 
 
 class ClockSampler:
@@ -131,6 +186,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def pct(x, q):
+    return float(np.percentile(np.asarray(x, dtype=np.float64), q)) if len(x) else None
+
+
 def make_stream(scale: int, batch: int, seed: int = 1):
     e = W.rmat(scale, 16, seed=seed)
     ins = W.shuffled(e, 11)
@@ -141,35 +200,41 @@ def make_stream(scale: int, batch: int, seed: int = 1):
 
 
 def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3, levels_per_group=0,
-                  sizes=(1_000_000, 100_000)):
+                  sizes=(1_000_000, 100_000), jump=False):
     """The experiments' Ins / Del / Mix protocols on the same graph, plain form,
     device-resident inputs: Ins all edges from empty and Del them all, in batches of
     1e6 and 1e5; Mix = 50/50 insert/delete batches of 1e6 on a 90 %-loaded graph
-    (untimed preload).  Per protocol: updates/s over the whole sequence and the
-    p50/p99 of the per-batch latency, both from CUDA events on the handle's stream."""
+    (untimed preload).  Per protocol: updates/s (submitted and valid) over the whole
+    sequence, the p50/p99 of the per-batch latency (CUDA events on the handle's
+    stream between consecutive synchronous calls: submit to completion, no host
+    staging since the batches are on the device), and the rounds and moves."""
     import torch
 
     def timed(g, calls):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
-        upd = 0
+        upd, sts = 0, []
         torch.cuda.synchronize()
         evs[0].record()
         for i, (fn, b) in enumerate(calls):
             fn(b)
             upd += b.shape[0]
             evs[i + 1].record()
+            sts.append(g.stats())
         torch.cuda.synchronize()
         lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(calls))]
         tot = evs[0].elapsed_time(evs[-1])
         return {"updates_per_s": upd / (tot / 1e3), "batches": len(calls),
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "valid_updates_per_s": sum(x["valid"] for x in sts) / (tot / 1e3),
+                "rounds": sum(x["rounds"] for x in sts), "moves": sum(x["moves"] for x in sts),
+                "rounds_run": sum(x["rounds"] - x["skipped_rounds"] for x in sts)}
 
     out = {}
     for B in sizes:
         tag = "1e6" if B == 1_000_000 else "1e5"
-        g = P.PLDS(n, levels_per_group=levels_per_group)
+        g = P.PLDS(n, levels_per_group=levels_per_group, jump=jump)
         out[f"ins_{tag}"] = timed(g, [(g.insert, ins_d[s:s + B]) for s in range(0, ins_d.shape[0], B)])
-        if B == sizes[0] and levels_per_group == 0:
+        if B == sizes[0] and levels_per_group == 0 and not jump:
             # the static approximate k-core (Algorithm 6) of the loaded graph
             d = torch.empty(n, dtype=torch.float64, device="cuda")
             g.static_coreness(1.0, out=d)
@@ -184,7 +249,7 @@ def run_protocols(P, n, e, ins_d, del_d, mix_batches=10, seed=3, levels_per_grou
         out[f"del_{tag}"] = timed(g, [(g.delete, del_d[s:s + B]) for s in range(0, del_d.shape[0], B)])
         g.close()
     pre, mixes = W.mix_stream(e, 1_000_000, mix_batches, load=0.9, seed=seed)
-    g = P.PLDS(n, levels_per_group=levels_per_group)
+    g = P.PLDS(n, levels_per_group=levels_per_group, jump=jump)
     pre_d = torch.from_numpy(pre).cuda()
     for s in range(0, pre_d.shape[0], 1_000_000):
         g.insert(pre_d[s:s + 1_000_000])
@@ -208,17 +273,19 @@ def cpu_sample(scale, ins, sample_batch=500_000):
     t0 = time.perf_counter()
     o.insert(b)
     dt = time.perf_counter() - t0
-    return {"value": b.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": b.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"first {b.shape[0]} edges of the first Ins batch of the same R-MAT scale-{scale} "
                       f"stream, applied as one batch to the empty graph ({dt:.1f} s on 1 host core; the "
                       f"full 10^6-edge batch takes minutes)"}
 
 
-def plain_config(args, n: int, m: int, world: int) -> dict:
-    """The workload of the default (plain-form) bench line; the reference arm reports the same."""
-    return {"workload": f"rmat{args.scale}_ef16_B{args.batch:.0e}_ins_del_cycle".replace("+0", ""),
+def plain_config(args, n: int, m: int, world: int, batch: int | None = None) -> dict:
+    """The workload of the default (plain-form) bench line at `batch` edges a step
+    (default: args.batch); the reference arm states the batch it ran."""
+    b = args.batch if batch is None else batch
+    return {"workload": f"rmat{args.scale}_ef16_B{b:.0e}_ins_del_cycle".replace("+0", ""),
             "graph": f"R-MAT scale {args.scale}, (.57,.19,.19,.05), edge factor 16, symmetrised, deduplicated",
-            "n": n, "m": m, "batch": args.batch, "delta": 0.4, "lambda": 3,
+            "n": n, "m": m, "batch": b, "delta": 0.4, "lambda": 3,
             "stream": "Ins all edges from empty, then Del all edges (cyclic)",
             "form": "plain: one synchronous launch sequence per batch",
             "l2": "no flush: graph state (~1 GB adjacency + arrays) is larger than the 129 MB L2",
@@ -250,12 +317,14 @@ def run_reference(args):
     upd = sum(step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
     v = upd / dt
+    cfg = plain_config(args, 1 << args.scale, int(e.shape[0]), int(os.environ.get("WORLD_SIZE", "1")), batch=b)
+    cfg["native_arm_batch"] = args.batch
+    cfg["stream"] = "Ins edges of the same stream from empty (the oracle takes minutes per 10^6-edge batch)"
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "impl": "reference",
-            "config": plain_config(args, 1 << args.scale, int(e.shape[0]), int(os.environ.get("WORLD_SIZE", "1"))),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                              "sample": f"the sequential CPU oracle as it stands, on 1 host core: {args.steps} "
                                        f"consecutive Ins batches of {b} edges of the same stream from the empty "
                                        f"graph, after {args.warmup} warm-up batches (a full {args.batch}-edge "
@@ -264,30 +333,184 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def make_batched(graphs: int, rounds: int, seed: int = 7):
-    """graphs Chung-Lu graphs (n log-uniform in [1e3,1e5], exponent U[2.1,2.8], average
-    degree U[4,32]); half of each graph's edges preloaded (shuffled), then `rounds`
-    mixed batches per graph, each inserting 0.5-5 % of its edges taken from the
-    absent pool and deleting as many present ones (1-10 % of its edges in total);
-    pools are queues, so a deleted edge can come back in a later round."""
-    rng = np.random.default_rng(seed)
-    ns, pre, rnds = [], [], [[] for _ in range(rounds)]
-    for i in range(graphs):
-        n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
-        e = W.chung_lu(n, int(n * rng.uniform(4, 32) / 2), rng.uniform(2.1, 2.8), seed=seed * 100003 + i)
-        e = e[rng.permutation(e.shape[0])]
-        half = e.shape[0] // 2
-        ns.append(n)
-        pre.append(np.ascontiguousarray(e[:half]))
-        present, absent = e[:half], e[half:]
-        for r in range(rounds):
-            k = max(1, int(rng.uniform(0.005, 0.05) * e.shape[0]))
-            k = min(k, present.shape[0], absent.shape[0])
-            ins, dele = absent[:k], present[:k]
-            rnds[r].append((np.ascontiguousarray(ins), np.ascontiguousarray(dele)))
-            absent = np.concatenate([absent[k:], dele])
-            present = np.concatenate([present[k:], ins])
+def _batched_graph(args):
+    """Graph i of the batched workload and its round batches, from its own seed:
+    n log-uniform in [1e3,1e5], Chung-Lu exponent U[2.1,2.8], average degree
+    U[4,32]; half of its edges preloaded (shuffled), then `rounds` mixed batches,
+    each inserting 0.5-5 % of its edges taken from the absent pool and deleting as
+    many present ones; the pools are queues, so a deleted edge can come back later."""
+    i, rounds, seed = args
+    rng = np.random.default_rng((seed, i))
+    n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+    e = W.chung_lu(n, int(n * rng.uniform(4, 32) / 2), rng.uniform(2.1, 2.8), seed=seed * 100003 + i)
+    e = e[rng.permutation(e.shape[0])]
+    half = e.shape[0] // 2
+    present, absent = e[:half], e[half:]
+    rs = []
+    for _ in range(rounds):
+        k = max(1, int(rng.uniform(0.005, 0.05) * e.shape[0]))
+        k = min(k, present.shape[0], absent.shape[0])
+        ins, dele = absent[:k], present[:k]
+        rs.append((np.ascontiguousarray(ins), np.ascontiguousarray(dele)))
+        absent = np.concatenate([absent[k:], dele])
+        present = np.concatenate([present[k:], ins])
+    return n, np.ascontiguousarray(e[:half]), rs
+
+
+def make_batched(graphs: int, rounds: int, seed: int = 7, procs: int | None = None):
+    """The batched form's workload: `graphs` independent graphs (see _batched_graph),
+    generated in parallel host processes (spawned: safe after the GPU is in use).
+    Returns (ns, preloads, rounds[r][i] = (insertions, deletions))."""
+    import multiprocessing as mp
+    procs = procs or min(graphs, os.cpu_count() or 1)
+    jobs = [(i, rounds, seed) for i in range(graphs)]
+    if procs > 1:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_batched_graph, jobs, chunksize=1)
+    else:
+        res = [_batched_graph(j) for j in jobs]
+    ns = [r[0] for r in res]
+    pre = [r[1] for r in res]
+    rnds = [[r[2][k] for r in res] for k in range(rounds)]
     return ns, pre, rnds
+
+
+def _oracle_batched_worker(work, warm, timed, barrier, queue):
+    """One host process of the batched form's CPU baseline: its graphs' preload and
+    warm-up rounds untimed, then the timed rounds between two barriers."""
+    from oracle import oracle as O
+    graphs = [(O.OraclePLDS(n), pre, rs) for n, pre, rs in work]
+    for o, pre, rs in graphs:
+        o.insert(pre)
+        for ins, dele in rs[:warm]:
+            o.insert(ins)
+            o.delete(dele)
+    barrier.wait()
+    t0 = time.perf_counter()
+    upd = 0
+    for o, pre, rs in graphs:
+        for ins, dele in rs[warm:warm + timed]:
+            o.insert(ins)
+            o.delete(dele)
+            upd += ins.shape[0] + dele.shape[0]
+    t1 = time.perf_counter()
+    queue.put((upd, t0, t1))
+
+
+def batched_cpu_baseline(ns, pre, rnds, warm: int, timed: int, every: int) -> dict:
+    """The oracle as P independent processes (P = host cores) over a sample of the
+    graphs (every `every`-th, split over the processes by the greedy size balance):
+    the same preload and warm-up rounds untimed, then `timed` rounds; updates/s =
+    the sampled updates over the wall time from the common start to the last end."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    sample = list(range(0, len(ns), every))
+    procs_n = max(1, min(os.cpu_count() or 1, len(sample)))
+    parts = shard_graphs([pre[i].shape[0] for i in sample], procs_n)
+    barrier, queue = ctx.Barrier(procs_n), ctx.Queue()
+    procs = []
+    for part in parts:
+        work = [(ns[sample[k]], pre[sample[k]], [rnds[r][sample[k]] for r in range(warm + timed)]) for k in part]
+        p = ctx.Process(target=_oracle_batched_worker, args=(work, warm, timed, barrier, queue))
+        p.start()
+        procs.append(p)
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    upd = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": upd / wall, "unit": UNIT, "cores": procs_n, "kind": "oracle", "cpu": host_cpu(),
+            "sample": f"{len(sample)} of the {len(ns)} graphs (every {every}th), {timed} mixed rounds after the "
+                      f"same preload and {warm} warm-up rounds, as {procs_n} independent oracle processes "
+                      f"(graphs split by size); {upd} updates in {wall:.2f} s wall"}
+
+
+def batched_results(P, ns, pre, rnds, warmup: int, tune_trials: int, plain_rounds: int,
+                    autotune: bool = True, cpu_every: int = 16, cpu_rounds: int = 2, local: int = 0) -> dict:
+    """The batched form on the given graphs (one launch per round of batches), the
+    same rounds with the set's default knobs, the plain form looping over the graphs,
+    and the oracle's CPU baseline."""
+    import torch
+    rounds = len(rnds)
+    e0, o0 = P.PLDSSet.pack([(p_, np.zeros((0, 2), np.int32)) for p_ in pre])
+    pre_dev = (torch.from_numpy(e0).cuda(), o0)
+    packed = [P.PLDSSet.pack(r) for r in rnds]
+    dev = [(torch.from_numpy(e).cuda(), o) for e, o in packed]
+    upd = [int(o[-1]) for _, o in packed]
+    w = min(warmup, rounds - 1)
+
+    def timed_set(tuning, clk=None):
+        """Preload, warm-up rounds, then the timed rounds; returns (seconds, set, per-round ms)."""
+        S = P.PLDSSet(ns)
+        if tuning:
+            S.tune(**tuning)
+        S.update(*pre_dev)
+        for r in range(w):
+            S.update(*dev[r])
+        torch.cuda.synchronize()
+        lat = []
+        t0 = time.perf_counter()
+        for r in range(w, rounds):
+            t1 = time.perf_counter()
+            S.update(*dev[r])
+            lat.append(1e3 * (time.perf_counter() - t1))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, S, lat
+
+    tuning, t_tune = None, 0.0
+    if autotune and w > 0:
+        probe = P.PLDSSet(ns)
+        t0 = time.perf_counter()
+        tuning = probe.autotune([pre_dev] + dev[:w], timed_from=1, max_trials=tune_trials)
+        t_tune = time.perf_counter() - t0
+        probe.close()
+    dt_default, S0, _ = timed_set(None)
+    S0.close()
+    with ClockSampler(local) as clk:
+        dt, S, lat = timed_set(tuning)
+    batched = sum(upd[w:]) / dt
+    # the plain form: one synchronous insert and delete call per graph, graphs one after another
+    G = [P.PLDS(n) for n in ns]
+    for g, p_ in zip(G, pre):
+        g.insert(torch.from_numpy(p_).cuda())
+    for r in range(w):
+        for g, (ins, dele) in zip(G, rnds[r]):
+            g.insert(torch.from_numpy(ins).cuda())
+            g.delete(torch.from_numpy(dele).cuda())
+    nplain = min(rounds - w, plain_rounds)
+    devr = [[(torch.from_numpy(i_).cuda(), torch.from_numpy(d_).cuda()) for i_, d_ in rnds[r]]
+            for r in range(w, w + nplain)]
+    torch.cuda.synchronize()
+    plat = []
+    t0 = time.perf_counter()
+    for rr in devr:
+        t1 = time.perf_counter()
+        for g, (ins, dele) in zip(G, rr):
+            g.insert(ins)
+            g.delete(dele)
+        plat.append(1e3 * (time.perf_counter() - t1))
+    torch.cuda.synchronize()
+    dtp = time.perf_counter() - t0
+    plain = sum(upd[w:w + nplain]) / dtp
+    same = all(np.array_equal(a.levels(), b.levels()) for a, b in zip(S.graphs, G)) if nplain == rounds - w else None
+    S.close()
+    for g in G:
+        g.close()
+    out = {"updates_per_s": batched, "rounds_timed": rounds - w, "warmup_rounds": w,
+           "round_ms": {"mean": 1e3 * dt / (rounds - w), "p50": pct(lat, 50), "p99": pct(lat, 99),
+                        "of": "host time of each round's call (submit to completion)"},
+           "clocks": clk.summary(),
+           "plain_loop": {"updates_per_s": plain, "rounds_timed": nplain,
+                          "round_ms": {"mean": 1e3 * dtp / nplain, "p50": pct(plat, 50), "p99": pct(plat, 99)}},
+           "speedup_vs_plain": batched / plain, "levels_equal_plain": same,
+           "autotune": {"knobs": tuning, "seconds": t_tune, "trials_max": tune_trials,
+                        "sample": "preload + warm-up rounds (untimed)",
+                        "default_knobs_updates_per_s": sum(upd[w:]) / dt_default},
+           "workload": {"graphs": len(ns), "total_vertices": int(sum(ns)),
+                        "updates_per_round": int(np.mean(upd))}}
+    if cpu_every:
+        out["cpu_baseline"] = batched_cpu_baseline(ns, pre, rnds, w, min(cpu_rounds, rounds - w), cpu_every)
+    return out
 
 
 def device_checks(P, g, n, present, tables):
@@ -418,83 +641,49 @@ def run_large(args):
 
 
 def run_batched(args):
+    """--form batched: one JSON line.  Under torchrun (N > 1 ranks) every rank takes
+    its share of the graphs by the greedy size balance and runs them as its own set;
+    value = the updates of all ranks over the slowest rank's time (no data-path
+    collective: the graphs are independent)."""
     import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
     from paper_2106_03824_gb300 import plds as P
-    torch.cuda.set_device(0)
     ns, pre, rnds = make_batched(args.graphs, args.rounds)
-    e0, o0 = P.PLDSSet.pack([(p_, np.zeros((0, 2), np.int32)) for p_ in pre])
-    pre_dev = (torch.from_numpy(e0).cuda(), o0)
-    packed = [P.PLDSSet.pack(r) for r in rnds]
-    dev = [(torch.from_numpy(e).cuda(), o) for e, o in packed]
-    upd = [int(o[-1]) for _, o in packed]
-    w = min(args.warmup, args.rounds - 1)
-
-    def timed_set(tuning):
-        """Preload, warm-up rounds, then the timed rounds; returns (seconds, set)."""
-        S = P.PLDSSet(ns)
-        if tuning:
-            S.tune(**tuning)
-        S.update(*pre_dev)
-        for r in range(w):
-            S.update(*dev[r])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for r in range(w, args.rounds):
-            S.update(*dev[r])
-        torch.cuda.synchronize()
-        return time.perf_counter() - t0, S
-
-    # knobs picked by the autotuner on the preload and warm-up rounds only
-    tuning = None
-    t_tune = 0.0
-    if not args.no_autotune and w > 0:
-        probe = P.PLDSSet(ns)
-        t0 = time.perf_counter()
-        tuning = probe.autotune([pre_dev] + dev[:w], timed_from=1, max_trials=args.tune_trials)
-        t_tune = time.perf_counter() - t0
-        probe.close()
-    dt_default, S0 = timed_set(None)
-    S0.close()
-    dt, S = timed_set(tuning)
-    lat = dt / (args.rounds - w)
-    batched = sum(upd[w:]) / dt
-    # the plain form: one synchronous insert and delete call per graph, graphs one after another
-    G = [P.PLDS(n) for n in ns]
-    for g, p_ in zip(G, pre):
-        g.insert(torch.from_numpy(p_).cuda())
-    for r in range(w):
-        for g, (ins, dele) in zip(G, rnds[r]):
-            g.insert(torch.from_numpy(ins).cuda())
-            g.delete(torch.from_numpy(dele).cuda())
-    nplain = min(args.rounds - w, args.plain_rounds)
-    devr = [[(torch.from_numpy(i_).cuda(), torch.from_numpy(d_).cuda()) for i_, d_ in rnds[r]]
-            for r in range(w, w + nplain)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for rr in devr:
-        for g, (ins, dele) in zip(G, rr):
-            g.insert(ins)
-            g.delete(dele)
-    torch.cuda.synchronize()
-    dtp = time.perf_counter() - t0
-    plain = sum(upd[w:w + nplain]) / dtp
-    same = all(np.array_equal(a.levels(), b.levels()) for a, b in zip(S.graphs, G)) if nplain == args.rounds - w else None
-    line = {"metric": "edge updates/s, batched form (one launch per round of batches)", "value": batched,
-            "unit": UNIT, "n_gpus": 1, "steps": args.rounds - w, "warmup": w, "ms_per_step": 1e3 * lat,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "form": "batched",
-            "config": {"workload": f"{args.graphs} Chung-Lu graphs, n log-uniform [1e3,1e5], exponent U[2.1,2.8], "
-                                   f"avg degree U[4,32], half preloaded, {args.rounds} mixed rounds of 1-10% of edges",
-                       "total_vertices": int(sum(ns)), "updates_per_round": int(np.mean(upd))},
-            "plain_loop": {"value": plain, "unit": UNIT, "rounds_timed": nplain,
-                           "ms_per_round": 1e3 * dtp / nplain},
-            "speedup_vs_plain": batched / plain, "levels_equal_plain": same,
-            "autotune": {"knobs": tuning, "seconds": t_tune, "trials_max": args.tune_trials,
-                         "sample": "preload + warm-up rounds (untimed)",
-                         "default_knobs_updates_per_s": sum(upd[w:]) / dt_default}}
-    print(json.dumps(line), flush=True)
+    mine = shard_graphs([p_.shape[0] for p_ in pre], world)[rank]
+    ns_r = [ns[i] for i in mine]
+    pre_r = [pre[i] for i in mine]
+    rnds_r = [[r[i] for i in mine] for r in rnds]
+    res = batched_results(P, ns_r, pre_r, rnds_r, args.warmup, args.tune_trials, args.plain_rounds,
+                          autotune=not args.no_autotune, cpu_every=16 if world == 1 else 0, local=local)
+    w = res["warmup_rounds"]
+    upd = sum(sum(i.shape[0] + d.shape[0] for i, d in rnds_r[r]) for r in range(w, args.rounds))
+    secs = upd / res["updates_per_s"]
+    if dist:
+        dist.barrier()
+    upd_all, secs_max = whole_job(dist, upd, secs, "cuda")
+    if rank == 0:
+        line = {"metric": "edge updates/s, batched form (one launch per round of batches)",
+                "value": upd_all / secs_max, "unit": UNIT, "n_gpus": world, "steps": args.rounds - w,
+                "warmup": w, "ms_per_step": 1e3 * secs_max / (args.rounds - w), "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "form": "batched",
+                "config": {"workload": f"{args.graphs} Chung-Lu graphs, n log-uniform [1e3,1e5], exponent "
+                                       f"U[2.1,2.8], avg degree U[4,32], half preloaded, {args.rounds} mixed rounds "
+                                       "of 1-10% of edges",
+                           "parallelism": f"graphs split over {world} ranks by size (greedy)"},
+                "rank0": res}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def make_serving_stream(e: np.ndarray, requests: int, seed: int = 5):
@@ -527,15 +716,40 @@ def make_serving_stream(e: np.ndarray, requests: int, seed: int = 5):
     return np.ascontiguousarray(pre), reqs
 
 
-def run_serving(args):
+def serving_cpu_baseline(n: int, reqs, budget: int = 200_000) -> dict:
+    """The oracle (1 core) on the stream's first requests until `budget` updates,
+    applied to an empty graph of the same n (building the preloaded 90 % state
+    would take the oracle over ten minutes)."""
+    from oracle import oracle as O
+    o = O.OraclePLDS(n)
+    upd, k = 0, 0
+    t0 = time.perf_counter()
+    for op, b in reqs:
+        if op == 2:
+            o.coreness()
+        elif op == 0:
+            o.insert(b)
+        else:
+            o.delete(b)
+        k += 1
+        upd += 0 if b is None else b.shape[0]
+        if upd >= budget:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
+            "sample": f"the first {k} requests ({upd} updates) of the same request stream applied to an empty "
+                      f"{n}-vertex graph by the sequential oracle, {dt:.1f} s on 1 host core"}
+
+
+def serving_results(P, n: int, m: int, requests: int, slots: int, local: int = 0, cpu: bool = True) -> dict:
+    """The serving form against the plain form on the same open-loop stream:
+    capacities with the whole stream submitted at once, then p50/p99 latency (from a
+    request's scheduled arrival to the host seeing it done) at 70 % and 90 % of the
+    plain form's capacity; estimates of the merged and the unmerged loops compared
+    per vertex on the final graph (the same edges, different batch boundaries)."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2106_03824_gb300 import plds as P
-    torch.cuda.set_device(0)
-    n, m = args.serve_n, args.serve_m
     e = W.chung_lu(n, m, 2.2, seed=1)
-    pre, reqs = make_serving_stream(e, args.requests)
+    pre, reqs = make_serving_stream(e, requests)
     pre_d = torch.from_numpy(pre).cuda()
     pinned = [(op, torch.from_numpy(b).pin_memory() if b is not None else None) for op, b in reqs]
     qout = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -566,9 +780,10 @@ def run_serving(args):
     results = {"plain_capacity_updates_per_s": upd_total / cap_s, "stream_seconds_back_to_back": cap_s}
 
     # capacity of the served forms: the whole stream submitted at once
+    final = {}
     for form, merge in (("served", -1), ("served_unmerged", 0)):
         g = preloaded()
-        sv = P.Server(g, slots=args.slots, max_batch=2_000_000, merge_max_edges=merge)
+        sv = P.Server(g, slots=slots, max_batch=2_000_000, merge_max_edges=merge)
         t0 = time.monotonic_ns()
         for op, b in pinned:
             if op == 2:
@@ -578,14 +793,20 @@ def run_serving(args):
         sv.drain()
         done = sv.poll(4096)
         sv.close()
+        final[form] = g.coreness()
         g.close()
         span = (max(r["done_ns"] for r in done) - t0) * 1e-9
         results[f"{form}_capacity_updates_per_s"] = upd_total / span
         results[f"{form}_device_batches_back_to_back"] = sum(r["batch_first"] == r["ticket"] for r in done)
+    a, b = final["served"], final["served_unmerged"]
+    nz = (a > 0) & (b > 0)
+    ratio = np.maximum(a[nz] / b[nz], b[nz] / a[nz])
+    results["merged_vs_unmerged_estimates"] = {
+        "max_ratio": float(ratio.max()) if ratio.size else 1.0, "mean_ratio": float(ratio.mean()) if ratio.size else 1.0,
+        "zero_mismatch": int(((a > 0) != (b > 0)).sum()),
+        "of": "per-vertex coreness estimates after the whole stream, continuous batching vs one batch per request"}
 
-    def pct(x, q):
-        return float(np.percentile(np.asarray(x) * 1e3, q))
-
+    clocks = {}
     for load in (0.7, 0.9):
         rate = load * len(reqs) / cap_s
         rng = np.random.default_rng(99)
@@ -594,59 +815,72 @@ def run_serving(args):
             g = preloaded()
             lat = np.zeros(len(reqs))
             sizes = []
-            if form == "plain":
-                t0 = time.monotonic_ns()
-                for i, (op, b) in enumerate(pinned):
-                    due = t0 + int(arrivals[i] * 1e9)
-                    while time.monotonic_ns() < due:
-                        pass
-                    plain_call(g, op, b)
-                    lat[i] = (time.monotonic_ns() - due) * 1e-9
-                span = (time.monotonic_ns() - t0) * 1e-9
-            else:
-                sv = P.Server(g, slots=args.slots, max_batch=2_000_000,
-                              merge_max_edges=-1 if form == "served" else 0)
-                done = {}
-                t0 = time.monotonic_ns()
-                for i, (op, b) in enumerate(pinned):
-                    due = t0 + int(arrivals[i] * 1e9)
-                    while time.monotonic_ns() < due:
+            with ClockSampler(local) as clk:
+                if form == "plain":
+                    t0 = time.monotonic_ns()
+                    for i, (op, b) in enumerate(pinned):
+                        due = t0 + int(arrivals[i] * 1e9)
+                        while time.monotonic_ns() < due:
+                            pass
+                        plain_call(g, op, b)
+                        lat[i] = (time.monotonic_ns() - due) * 1e-9
+                    span = (time.monotonic_ns() - t0) * 1e-9
+                else:
+                    sv = P.Server(g, slots=slots, max_batch=2_000_000, merge_max_edges=-1 if form == "served" else 0)
+                    done = {}
+                    t0 = time.monotonic_ns()
+                    for i, (op, b) in enumerate(pinned):
+                        due = t0 + int(arrivals[i] * 1e9)
+                        while time.monotonic_ns() < due:
+                            for r in sv.poll():
+                                done[r["ticket"]] = r
+                        if op == 2:
+                            sv.submit(2, out=qout.numpy())
+                        else:
+                            sv.submit(op, edges=b)
+                    while len(done) < len(reqs):
                         for r in sv.poll():
                             done[r["ticket"]] = r
-                    if op == 2:
-                        sv.submit(2, out=qout.numpy())
-                    else:
-                        sv.submit(op, edges=b)
-                while len(done) < len(reqs):
-                    for r in sv.poll():
-                        done[r["ticket"]] = r
-                span = (max(r["done_ns"] for r in done.values()) - t0) * 1e-9
-                for i in range(len(reqs)):
-                    lat[i] = (done[i]["done_ns"] - (t0 + int(arrivals[i] * 1e9))) * 1e-9
-                sizes = [r["batch_size"] for r in done.values() if r["batch_first"] == r["ticket"]]
-                sv.close()
+                    span = (max(r["done_ns"] for r in done.values()) - t0) * 1e-9
+                    for i in range(len(reqs)):
+                        lat[i] = (done[i]["done_ns"] - (t0 + int(arrivals[i] * 1e9))) * 1e-9
+                    sizes = [r["batch_size"] for r in done.values() if r["batch_first"] == r["ticket"]]
+                    sv.close()
             g.close()
+            clocks[f"{form}@{int(load * 100)}%"] = clk.summary()
             results[f"{form}@{int(load * 100)}%"] = {
-                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(lat.mean() * 1e3),
+                "p50_ms": pct(lat * 1e3, 50), "p99_ms": pct(lat * 1e3, 99), "mean_ms": float(lat.mean() * 1e3),
                 "updates_per_s": upd_total / span, "makespan_s": span,
                 **({"device_batches": len(sizes), "max_requests_per_batch": int(max(sizes))} if sizes else {})}
-    best = results["served@90%"]
+    out = {"capacity_updates_per_s": results["served_capacity_updates_per_s"],
+           "p50_ms_at_90pct": results["served@90%"]["p50_ms"], "p99_ms_at_90pct": results["served@90%"]["p99_ms"],
+           "plain": {"capacity_updates_per_s": results["plain_capacity_updates_per_s"],
+                     "p50_ms_at_90pct": results["plain@90%"]["p50_ms"],
+                     "p99_ms_at_90pct": results["plain@90%"]["p99_ms"]},
+           "workload": {"graph": f"Chung-Lu n={n}, m={e.shape[0]}, exponent 2.2, 90% preloaded",
+                        "requests": len(reqs), "updates": upd_total, "slots": slots,
+                        "stream": "sizes log-uniform [10,1e6], 50/50 Ins/Del, coreness query every 20 batches, "
+                                  "Poisson arrivals at 70% and 90% of the plain form's capacity, inputs in "
+                                  "pinned host memory",
+                        "forms": "served = continuous batching (merged runs of waiting requests, logged "
+                                 "schedule); served_unmerged = the same loop, one batch per request"},
+           "results": results, "clocks": clocks}
+    if cpu:
+        out["cpu_baseline"] = serving_cpu_baseline(n, reqs)
+    return out
+
+
+def run_serving(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_03824_gb300 import plds as P
+    torch.cuda.set_device(0)
+    res = serving_results(P, args.serve_n, args.serve_m, args.requests, args.slots)
     line = {"metric": "edge updates/s and p50/p99 batch latency, serving form (device-resident request loop)",
-            "value": results["served_capacity_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
-            "warmup": 0, "p50_ms_at_90pct": best["p50_ms"], "p99_ms_at_90pct": best["p99_ms"],
-            "plain": {"capacity_updates_per_s": results["plain_capacity_updates_per_s"],
-                      "p50_ms_at_90pct": results["plain@90%"]["p50_ms"],
-                      "p99_ms_at_90pct": results["plain@90%"]["p99_ms"]},
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "form": "serving",
-            "config": {"workload": f"Chung-Lu n={n}, m={e.shape[0]}, exponent 2.2, 90% preloaded; "
-                                   f"{len(reqs)} requests, sizes log-uniform [10,1e6], 50/50 Ins/Del, "
-                                   "coreness query every 20 batches, Poisson arrivals at 70% and 90% of "
-                                   "the plain form's capacity; inputs in pinned host memory; "
-                                   "served = continuous batching (merged runs, logged schedule), "
-                                   "served_unmerged = same loop with unchanged batch boundaries",
-                       "slots": args.slots, "updates": upd_total},
-            "results": results}
+            "value": res["capacity_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": res["workload"]["requests"],
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "form": "serving", "config": {"workload": res["workload"]["graph"]}, **res}
     print(json.dumps(line), flush=True)
 
 
@@ -663,6 +897,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-protocols", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="leave the serving and batched forms out of the line")
     ap.add_argument("--dump-recs", default=None, help="write per-step kernel records (JSON) to this path")
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving", "large"])
     ap.add_argument("--large-n", type=int, default=41_700_000)
@@ -706,7 +941,7 @@ def main():
     del_d = torch.from_numpy(del_h).cuda()
     core_d = torch.empty(n, dtype=torch.float64, device="cuda")
 
-    def run_steps(g, k0, count, host=False, pinned=None, core_h=None):
+    def run_steps(g, k0, count, host=False, pinned=None, core_h=None, lat=None):
         upd, recs = 0, []
         for k in range(k0, k0 + count):
             kind, a, b = steps[k % len(steps)]
@@ -714,8 +949,11 @@ def main():
                 src = pinned[kind][a:b]
             else:
                 src = (ins_d if kind == "ins" else del_d)[a:b]
-            (g.insert if kind == "ins" else g.delete)(src)
-            recs.append(g.stats())
+            t1 = time.perf_counter()
+            (g.insert if kind == "ins" else g.delete)(src)  # synchronous: returns when the batch is done
+            if lat is not None:
+                lat.append(1e3 * (time.perf_counter() - t1))
+            recs.append((kind, g.stats()))
             g.coreness(core_h if host else core_d)
             upd += b - a
         return upd, recs
@@ -727,9 +965,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    host_lat = []
     with ClockSampler(local) as clk:
         ev0.record()
-        upd, recs = run_steps(g, args.warmup, args.steps)
+        upd, recs = run_steps(g, args.warmup, args.steps, lat=host_lat)
         ev1.record()
         torch.cuda.synchronize()
     if dist:
@@ -738,26 +977,39 @@ def main():
     launches = g.stats()["launches"] - launches0
     g.close()
     upd_all, t_max_s = whole_job(dist, upd, ms / 1e3, "cuda")
+    valid_all, _ = whole_job(dist, sum(r["valid"] for _, r in recs), ms / 1e3, "cuda")
     t_max = t_max_s * 1e3
     value = upd_all / t_max_s
 
-    # roofline of the batch kernel: algorithmic bytes / event-timed kernel duration
-    kern_ns = sum(r["kernel_ns"] for r in recs)
-    abytes = sum(algo_bytes(r) for r in recs)
+    # roofline of the batch kernel: algorithmic bytes of the executed work / event-timed kernel duration
+    kern_ns = sum(r["kernel_ns"] for _, r in recs)
+    abytes = sum(algo_bytes(r, kind) for kind, r in recs)
+    sbytes = sum(algo_bytes_survey(r) for _, r in recs)
+    xbytes = sum(algo_bytes_with_skipped(r, kind) for kind, r in recs)
     achieved = abytes / (kern_ns / 1e9) / 1e9 if kern_ns else None
+    s_achieved = sbytes / (kern_ns / 1e9) / 1e9 if kern_ns else None
     peak, peak_src = measured_peaks()
     traffic = None
     if NCU_TRAFFIC["kernel_sha"] == kernel_sha() and NCU_TRAFFIC["dram_per_algo_byte"]:
         traffic = NCU_TRAFFIC["dram_per_algo_byte"] * abytes / len(recs)
     if args.dump_recs:  # per timed step: the batch kernel's algorithmic bytes (matches ncu launch lists)
         with open(args.dump_recs, "w") as f:
-            json.dump([{"algo_bytes": algo_bytes(r), "kernel_ns": r["kernel_ns"], "launches": r["launches"],
-                        "valid": r["valid"]} for r in recs], f)
+            json.dump([{"kind": kind, "algo_bytes": algo_bytes(r, kind), "algo_bytes_survey": algo_bytes_survey(r),
+                        "kernel_ns": r["kernel_ns"], "launches": r["launches"], "valid": r["valid"]}
+                       for kind, r in recs], f)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": "k_batch_grid", "peak_source": peak_src,
             "kernel_ms_per_launch": kern_ns / 1e6 / len(recs),
-            "algo_bytes_per_launch": abytes / len(recs)}
+            "algo_bytes_per_launch": abytes / len(recs),
+            "definition": "executed work, insertion moves at their up-degree (up-neighbours examined)",
+            "survey_definition": {"algo_bytes_per_launch": sbytes / len(recs), "achieved": s_achieved,
+                                  "frac": (s_achieved / peak) if s_achieved else None,
+                                  "definition": "executed work, every move at its degree + 8 B per affected "
+                                                "neighbour"},
+            "with_skipped_rounds": {"algo_bytes_per_launch": xbytes / len(recs),
+                                    "note": "the skipped pure rounds counted as Algorithm 2 would run them; "
+                                            "not a bandwidth figure"}}
 
     # e2e: the same steps through the C ABI with pinned host buffers (H2D of the batch
     # and D2H of every vertex's coreness inside the timed region), fresh graph
@@ -780,9 +1032,9 @@ def main():
         e2e = {"value": upd2_all / dt2, "unit": UNIT, "h2d_bytes_per_step": 8 * upd2 / args.steps,
                "d2h_bytes_per_step": 8 * n}
 
-    # per-batch latency of the timed steps (kernel time of each call)
-    lat_ms = [r["kernel_ns"] / 1e6 for r in recs]
+    lat_ms = [r["kernel_ns"] / 1e6 for _, r in recs]
     protocols = None
+    forms = None
     if world == 1 and not args.no_protocols:
         protocols = run_protocols(P, n, e, ins_d, del_d)
         # the paper's optimised variant: ceil(log_{1+delta} m / 50) levels per group
@@ -790,14 +1042,26 @@ def main():
         protocols["plds_opt"] = {"levels_per_group": lg_opt,
                                  **run_protocols(P, n, e, ins_d, del_d, levels_per_group=lg_opt,
                                                  sizes=(1_000_000,))}
+        # the experiments' filter+sort insertion variant (same levels, its own rounds)
+        protocols["jump"] = run_protocols(P, n, e, ins_d, del_d, jump=True)
+    if world == 1 and not args.no_forms:
+        del ins_d, del_d
+        torch.cuda.empty_cache()
+        forms = {"serving": serving_results(P, args.serve_n, args.serve_m, args.requests, args.slots, local,
+                                            cpu=not args.no_cpu_baseline)}
+        ns_b, pre_b, rnds_b = make_batched(args.graphs, args.rounds)
+        forms["batched"] = batched_results(P, ns_b, pre_b, rnds_b, 3, min(args.tune_trials, 8), args.plain_rounds,
+                                           cpu_every=0 if args.no_cpu_baseline else 16, local=local)
 
     phases = {}
     for kind in ("ins", "del"):
-        sel = [(r, steps[(args.warmup + i) % len(steps)]) for i, r in enumerate(recs)
+        sel = [(r, steps[(args.warmup + i) % len(steps)]) for i, (_, r) in enumerate(recs)
                if steps[(args.warmup + i) % len(steps)][0] == kind]
         if sel:
             ns = sum(r["kernel_ns"] for r, _ in sel)
-            phases[kind] = {"steps": len(sel), "updates_per_s_kernel": sum(s[2] - s[1] for _, s in sel) / (ns / 1e9)}
+            phases[kind] = {"steps": len(sel), "updates_per_s_kernel": sum(s[2] - s[1] for _, s in sel) / (ns / 1e9),
+                            "rounds_counted": sum(r["rounds"] for r, _ in sel),
+                            "rounds_run": sum(r["rounds"] - r["skipped_rounds"] for r, _ in sel)}
 
     if rank != 0:
         if dist:
@@ -816,10 +1080,14 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "valid_updates_per_s": valid_all / t_max_s,
         "phases": phases,
-        "batch_latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                             "of": "batch kernel time of each timed step"},
+        "batch_latency_ms": {"kernel": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99)},
+                             "submit_to_completion": {"p50": pct(host_lat, 50), "p99": pct(host_lat, 99)},
+                             "of": "each timed step's batch call: its kernel (CUDA events), and the host time "
+                                   "from the call to its return (the call is synchronous)"},
         "protocols": protocols,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
     if dist:

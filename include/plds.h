@@ -75,6 +75,16 @@ typedef struct plds_stats {
     int64_t launches;      /* kernels launched by this handle since creation */
     int64_t up_visits;     /* insertion: up-neighbours of moving vertices, the sum of their
                               up-degrees over the moves (what a move must examine) */
+    int64_t affected;      /* neighbours whose up- or up*-degree a move changed, summed over
+                              the moves (the counter updates the moves made) */
+    /* Insertion rounds that change nothing but the level of the same climbing set
+       (no neighbour outside the set on the levels passed, no other candidate) are
+       counted, not run: of the rounds, moves, visits and up_visits above, these
+       many belong to such skipped rounds. */
+    int64_t skipped_rounds;
+    int64_t skipped_moves;
+    int64_t skipped_visits;
+    int64_t skipped_up_visits;
 } plds_stats_t;
 
 /* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */
@@ -169,6 +179,12 @@ int plds_batch_delete(plds_t *h, const int32_t *edges, int64_t B);
  *     the previous call's contents; calls that overlap on the GPU (another handle
  *     on another stream, another host thread) race and must be serialised by the
  *     caller.
+ *   - These calls do not track orientation: after one, plds_flips and
+ *     plds_oriented_updates return PLDS_EINVAL until the next regular batch call
+ *     made with tuning.track_orientation set.
+ *   - The looked-up address belongs to the device's current context: the library
+ *     must not be used across a cudaDeviceReset of that device (the reset also
+ *     invalidates every handle on it).
  */
 int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int32_t is_delete);
 

@@ -427,14 +427,24 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     return g;
 }
 
+// A kernel's dynamic shared-memory limit is an attribute of the kernel on one
+// device: raise it once per device (any host thread may drive handles on any
+// device), the first time a kernel launches there.
+constexpr int kAttrDevices = 128;
+
+template <class K>
+static void raise_smem_limit(K kernel, std::atomic<bool> (&done)[kAttrDevices], int device) {
+    if (device >= 0 && device < kAttrDevices && done[device].load(std::memory_order_acquire)) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (device >= 0 && device < kAttrDevices) done[device].store(true, std::memory_order_release);
+}
+
+static std::atomic<bool> g_attr_batch[kAttrDevices];
+
 static int launch_batch(plds *h, const GraphCtx &g) {
     const int threads = block_threads(h);
     const size_t smem = smem_bytes(threads);
-    static thread_local bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_batch_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
+    raise_smem_limit(k_batch_grid, g_attr_batch, h->device);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_grid, threads, smem);
     int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : 1;
@@ -536,6 +546,11 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
     h->last.up_visits = (int64_t)c.st[kStUpVisits];
+    h->last.affected = (int64_t)c.st[kStAffected];
+    h->last.skipped_rounds = (int64_t)c.st[kStSkipRounds];
+    h->last.skipped_moves = (int64_t)c.st[kStSkipMoves];
+    h->last.skipped_visits = (int64_t)c.st[kStSkipVisits];
+    h->last.skipped_up_visits = (int64_t)c.st[kStSkipUpVisits];
     h->orient_ok = h->tune.track_orientation != 0;
     return PLDS_OK;
 }
@@ -1301,7 +1316,9 @@ static std::mutex g_static_mu;
 static unsigned char *g_static_addr[kMaxDevices];
 
 // Device address of g_static_scratch on the current device (looked up once per
-// device; in host code the symbol itself is only a host-side stand-in).
+// device; in host code the symbol itself is only a host-side stand-in).  The
+// address belongs to the device's context: after cudaDeviceReset it is stale, as
+// is every handle created before the reset.
 static unsigned char *static_scratch(int device) {
     if (device < 0 || device >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lk(g_static_mu);
@@ -1341,13 +1358,15 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
         cudaMemsetAsync(h->stamp.p, 0, sizeof(int32_t) * (size_t)h->n, h->stream);
         h->stamp_base = 1;
     }
-    // what must start empty: control words, the key set, the level histogram
+    // what must start empty: control words, the key set (as large as the batch
+    // needs: a power of two >= 2B, so small batches clear little), the level histogram
+    const int64_t hc = std::min<int64_t>(kStaticHcap, pow2_at_least(2 * std::max<int64_t>(B, 1024)));
     cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream);
-    cudaMemsetAsync(base + kStOffHset, 0xff, 8 * (size_t)kStaticHcap, h->stream);
+    cudaMemsetAsync(base + kStOffHset, 0xff, 8 * (size_t)hc, h->stream);
     if (op == kOpInsert) cudaMemsetAsync(h->bins.p, 0, sizeof(int32_t) * ((size_t)h->T.K + 1), h->stream);
     GraphCtx g = make_ctx(h, op, dedges, B);
     g.hset = reinterpret_cast<unsigned long long *>(base + kStOffHset);
-    g.hcap = kStaticHcap;
+    g.hcap = hc;
     g.ukeys = reinterpret_cast<unsigned long long *>(base + kStOffUkeys);
     g.vkeys = reinterpret_cast<unsigned long long *>(base + kStOffVkeys);
     g.touched = reinterpret_cast<int32_t *>(base + kStOffTouched);
@@ -1369,6 +1388,9 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     const Ctl &c = h->host_ctl;
     h->last.err_bits = c.err;
     h->last.err_site = c.err_site;
+    h->last.err_info[0] = c.err_info[0];
+    h->last.err_info[1] = c.err_info[1];
+    h->last.err_info[2] = c.err_info[2];
     if (c.err & kErrTimeout) {
         h->poisoned = true;
         return set_status(PLDS_ETIMEOUT);
@@ -1392,6 +1414,11 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     h->last.dl_visits = (int64_t)c.st[kStDlVisits];
     h->last.slots_scanned = (int64_t)c.st[kStSlotsScanned];
     h->last.up_visits = (int64_t)c.st[kStUpVisits];
+    h->last.affected = (int64_t)c.st[kStAffected];
+    h->last.skipped_rounds = (int64_t)c.st[kStSkipRounds];
+    h->last.skipped_moves = (int64_t)c.st[kStSkipMoves];
+    h->last.skipped_visits = (int64_t)c.st[kStSkipVisits];
+    h->last.skipped_up_visits = (int64_t)c.st[kStSkipUpVisits];
     return set_status(PLDS_OK);
 }
 
@@ -1670,6 +1697,11 @@ extern "C" int plds_set_update(plds_set_t *s, const int32_t *edges, const int64_
                 h->last.dl_visits += (int64_t)c->st[kStDlVisits];
                 h->last.slots_scanned += (int64_t)c->st[kStSlotsScanned];
                 h->last.up_visits += (int64_t)c->st[kStUpVisits];
+                h->last.affected += (int64_t)c->st[kStAffected];
+                h->last.skipped_rounds += (int64_t)c->st[kStSkipRounds];
+                h->last.skipped_moves += (int64_t)c->st[kStSkipMoves];
+                h->last.skipped_visits += (int64_t)c->st[kStSkipVisits];
+                h->last.skipped_up_visits += (int64_t)c->st[kStSkipUpVisits];
             }
             const int64_t bi = offsets[2 * gi + 1] - offsets[2 * gi], bd = offsets[2 * gi + 2] - offsets[2 * gi + 1];
             h->last.duplicates = (bi > 0 ? bi - (int64_t)ci.st[kStSelfLoops] - (int64_t)ci.ucount : 0) +
@@ -2141,11 +2173,8 @@ static int server_launch(plds_server *sv) {
     plds *h = sv->h;
     const int threads = block_threads(h);
     const size_t smem = smem_bytes(threads);
-    static thread_local bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<bool> attr_serve[kAttrDevices];
+    raise_smem_limit(k_serve, attr_serve, h->device);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, threads, smem);
     const int per_sm = h->tune.blocks_per_sm > 0 ? std::min(h->tune.blocks_per_sm, occ) : 1;

@@ -1019,7 +1019,8 @@ __device__ __forceinline__ int32_t level_flag(int32_t l) { return (l & 1) ? kFla
 
 // Effects of a mover of level l on its neighbour w (level word raw).  Returns bit 0
 // if w became a mover of level l + 1 here, bit 1 if w stays on level l + 1 or above
-// after the round (an entry of the mover's up-list for its next move).  Movers of
+// after the round (an entry of the mover's up-list for its next move), bit 2 if one
+// of w's counters changed (a neighbour the move affected).  Movers of
 // l read as flagged words on levels lmo .. l + 1 (lmo = l unless pure rounds were
 // just skipped); low gets the lowest level above l of a neighbour that is no mover.
 __device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t lmo,
@@ -1034,9 +1035,11 @@ __device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t 
     if (f < l) return 0;
     low = min(low, f);
     if (f == l + 1) {
-        if (atomicAdd(&g.up[w], 1) == cut_next) return 2 | (!(atomicOr(&g.level[w], fnext) & fnext) ? 1 : 0);
+        if (atomicAdd(&g.up[w], 1) == cut_next) return 6 | (!(atomicOr(&g.level[w], fnext) & fnext) ? 1 : 0);
+        return 6;
     } else if (f == l + 2) {
         atomicAdd(&g.upstar[w], 1);
+        return 6;
     }
     return 2;
 }
@@ -1142,6 +1145,7 @@ __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &s
 template <class Team>
 __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0, upv = 0;
+    unsigned aff = 0;  // neighbours whose counters a move changed
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     const int32_t nlev = g.ctl->nlev;
@@ -1239,7 +1243,9 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         ideg += ws[q] >= 0;
-                        if (ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cnt_l, low) & 1) push |= 1u << q;
+                        const int r = ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cnt_l, low);
+                        if (r & 1) push |= 1u << q;
+                        aff += (r >> 2) & 1;
                     }
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
                     marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
@@ -1288,6 +1294,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     const int r = ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cl4[q >> 2], low);
                     if (r & 1) push |= 1u << q;
                     if (r & 2) keep |= 1u << q;
+                    aff += (r >> 2) & 1;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
@@ -1465,10 +1472,17 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 if (j >= 2) {
                     skip = (int32_t)j;
                     if (T.leader()) {
+                        const unsigned long long jm = (unsigned long long)j * (unsigned long long)m;
+                        const unsigned long long jv = (unsigned long long)j * g.ctl->isdeg[nxt];
+                        const unsigned long long ju = (unsigned long long)j * g.ctl->isup[nxt];
                         atomicAdd(&g.ctl->st[kStRounds], (unsigned long long)j);
-                        atomicAdd(&g.ctl->st[kStMoves], (unsigned long long)j * (unsigned long long)m);
-                        atomicAdd(&g.ctl->st[kStVisits], (unsigned long long)j * g.ctl->isdeg[nxt]);
-                        atomicAdd(&g.ctl->st[kStUpVisits], (unsigned long long)j * g.ctl->isup[nxt]);
+                        atomicAdd(&g.ctl->st[kStMoves], jm);
+                        atomicAdd(&g.ctl->st[kStVisits], jv);
+                        atomicAdd(&g.ctl->st[kStUpVisits], ju);
+                        atomicAdd(&g.ctl->st[kStSkipRounds], (unsigned long long)j);
+                        atomicAdd(&g.ctl->st[kStSkipMoves], jm);
+                        atomicAdd(&g.ctl->st[kStSkipVisits], jv);
+                        atomicAdd(&g.ctl->st[kStSkipUpVisits], ju);
                     }
                     lmo = l;
                     l += skip;
@@ -1500,10 +1514,12 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
     upv = warp_sum64(upv);
+    const unsigned long long affs = warp_sum64(aff);
     if (lane == 0) {
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
         atomicAdd(&g.ctl->st[kStUpVisits], upv);
+        if (affs) atomicAdd(&g.ctl->st[kStAffected], affs);
     }
     return T.sync();
 }
@@ -1799,13 +1815,14 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
 // w must be pushed for a desire-level recheck, 2 if that depends on w being
 // pending (its dlv decides).
 __device__ __forceinline__ int del_effect(const GraphCtx &g, int32_t w, int32_t lw, int32_t l, int32_t pv, int &cu,
-                                          int &cs) {
+                                          int &cs, unsigned &aff) {
     if (!valid_id(g, w)) return 0;
     cu += lw >= l;
     cs += lw >= l - 1;
     if (lw <= l) return 0;
     if (lw <= pv) atomicSub(&g.up[w], 1);
     if (lw - 1 > l && lw - 1 <= pv) atomicSub(&g.upstar[w], 1);
+    aff += lw <= pv + 1;  // w lost an up- or up*-neighbour
     if (lw < l + 2) return 0;
     return lw - 1 <= pv ? 1 : 2;
 }
@@ -1814,6 +1831,7 @@ template <class Team>
 __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base, const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist,
                            int32_t *wsm, RoundStage st) {
     unsigned long long visits = 0, scanned = 0, evals = 0, evisits = 0;
+    unsigned aff = 0;  // neighbours whose counters a move changed
     const int lane = lane_id();
     const int4 *pool4 = reinterpret_cast<const int4 *>(g.slots);
     for (int r = 0;; ++r) {
@@ -1913,7 +1931,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     visits += ws[k] >= 0;
-                    const int e = del_effect(g, ws[k], lv[k], l, it.w, cu, cs);
+                    const int e = del_effect(g, ws[k], lv[k], l, it.w, cu, cs, aff);
                     if (e == 1) push |= 1u << k;
                     if (e == 2) maybe |= 1u << k;
                 }
@@ -1952,7 +1970,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 visits += ws[k] >= 0;
-                const int e = del_effect(g, ws[k], lv[k], l, it[k >> 2].w, cu4[k >> 2], cs4[k >> 2]);
+                const int e = del_effect(g, ws[k], lv[k], l, it[k >> 2].w, cu4[k >> 2], cs4[k >> 2], aff);
                 if (e == 1) push |= 1u << k;
                 if (e == 2) maybe |= 1u << k;
             }
@@ -1999,9 +2017,11 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
     }
     visits = warp_sum64(visits);
     scanned = warp_sum64(scanned);
+    const unsigned long long affs = warp_sum64(aff);
     if (lane == 0) {
         atomicAdd(&g.ctl->st[kStVisits], visits);
         atomicAdd(&g.ctl->st[kStSlotsScanned], scanned);
+        if (affs) atomicAdd(&g.ctl->st[kStAffected], affs);
     }
     if (evals) {
         atomicAdd(&g.ctl->st[kStDlEvals], evals);
@@ -2022,13 +2042,14 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
 //
 // Violators wait in a pending list {v, level} (each vertex at most once: a vertex
 // is listed when it starts to violate and stays a violator until its round).
-// Round r, two team barriers:
+// Round r, three team barriers:
 //   A: the previous round's movers lose their flag; the pending entries on l
 //      become this round's movers (flag of r's parity in the level word, listed in
-//      TL[r mod 3]), the others carry over; the warp that takes a mover computes
-//      its target from a histogram of its neighbours' levels above l (levels read
-//      before any move of the round: the flags are masked), a block does it for a
-//      large table; targets go to dlv.
+//      TL[r mod 3]), the others stay (marked in place; the list is rewritten once
+//      most of it has been taken); then one warp per mover computes its target from
+//      a histogram of its neighbours' levels above l (levels read before any move
+//      of the round: the flags are masked), a block per large table; targets go to
+//      dlv.
 //   B: every mover scans its table once more: a neighbour that is a mover counts
 //      at its target, any other at its level; a non-mover w on level lw gains an
 //      up-neighbour if l < lw <= t and an up*-neighbour if l + 1 < lw <= t + 1, and
@@ -2103,27 +2124,35 @@ __device__ int32_t jump_target(const GraphCtx &g, int32_t v, int32_t l, const in
     return g.K - 1;  // not reached: the top group's bound is n
 }
 
-// Append the lanes' {v, level} with pred to pending list p (warp-collective).
-__device__ __forceinline__ void jump_push(const GraphCtx &g, int p, bool pred, int32_t v, int32_t lv) {
-    const int pos = warp_append(&g.ctl->jpend[p], pred);
+// Append the lanes' {v, level} with pred to pending list pl (warp-collective) and
+// fold their levels into the next round's minimum (slot ps); other: the entries are
+// not movers of this round staying on the next level.
+__device__ __forceinline__ void jump_push(const GraphCtx &g, int pl, int ps, bool pred, int32_t v, int32_t lv,
+                                          bool other) {
+    const int pos = warp_append(&g.ctl->jpend[pl], pred);
     if (pred) {
-        if (pos < 2 * g.n) g.P[p][pos] = make_int4(v, lv, 0, 0);
+        if (pos < 2 * g.n) g.P[pl][pos] = make_int4(v, lv, 0, 0);
         else report(g, kErrListOverflow, 20, pos, v, lv);
     }
     const int32_t mn = (int32_t)__reduce_min_sync(kFull, pred ? (unsigned)lv : (unsigned)kInf);
-    if (lane_id() == 0 && mn < kInf) atomicMax(&g.ctl->jnext_c[p], kInf - mn);
+    if (lane_id() == 0 && mn < kInf) {
+        atomicMax(&g.ctl->jnext_c[ps], kInf - mn);
+        if (other) atomicMax(&g.ctl->jother_c[ps], kInf - mn);
+    }
 }
 
 // Phase B for one mover v (old level l, target tv, round flag flr): warp, or
-// block when blk.  Returns its degree (visits); red: 2 ints of block scratch.
+// block when blk; new pending entries go to list pl, the round's totals to slot p.
+// Returns its degree (visits); red: 4 ints of block scratch.
 template <bool blk>
-__device__ int32_t jump_apply(const GraphCtx &g, int32_t v, int32_t l, int32_t tv, int32_t flr, int p,
-                              const int32_t *sh_upmax, int32_t *red) {
+__device__ int32_t jump_apply(const GraphCtx &g, int32_t v, int32_t l, int32_t tv, int32_t flr, int pl, int p,
+                              const int32_t *sh_upmax, int32_t *red, unsigned *aff) {
     const int32_t ng = g.cap[v] >> 2;
     const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[v]);
     const int start = blk ? (int)threadIdx.x : lane_id();
     const int stride = blk ? (int)blockDim.x : 32;
     int cu = 0, cs = 0, dg = 0;
+    int32_t low = kInf;  // lowest level above l of a neighbour that is no mover
     const int ng_iter = blk ? ((ng + stride - 1) / stride) * stride : ((ng + 31) & ~31);
     for (int j = start; j < ng_iter; j += stride) {  // every lane of a warp runs every step
         const int4 q = j < ng ? t4[j] : empty4();
@@ -2143,40 +2172,56 @@ __device__ int32_t jump_apply(const GraphCtx &g, int32_t v, int32_t l, int32_t t
                 } else {
                     lw = raw[u] & kLevelMask;
                     fw = lw;
+                    if (lw > l) low = min(low, lw);
                     if (l < lw && lw <= tv) push = atomicAdd(&g.up[ws[u]], 1) == sh_upmax[lw / g.Lg];
                     if (l + 1 < lw && lw <= tv + 1) atomicAdd(&g.upstar[ws[u]], 1);
+                    *aff += l < lw && lw <= tv + 1;
                 }
                 cu += fw >= tv;
                 cs += fw >= tv - 1;
             }
-            if (__any_sync(kFull, push)) jump_push(g, p, push, ws[u], lw);
+            if (__any_sync(kFull, push)) jump_push(g, pl, p, push, ws[u], lw, true);
         }
     }
     cu = warp_sum(cu);
     cs = warp_sum(cs);
     dg = warp_sum(dg);
+    low = (int32_t)__reduce_min_sync(kFull, (unsigned)low);
     if (blk) {
-        if (threadIdx.x == 0) red[0] = red[1] = red[2] = 0;
+        if (threadIdx.x == 0) {
+            red[0] = red[1] = red[2] = 0;
+            red[3] = kInf;
+        }
         __syncthreads();
         if (lane_id() == 0) {
             atomicAdd(&red[0], cu);
             atomicAdd(&red[1], cs);
             atomicAdd(&red[2], dg);
+            atomicMin(&red[3], low);
         }
         __syncthreads();
         cu = red[0];
         cs = red[1];
         dg = red[2];
+        low = red[3];
         __syncthreads();
     }
     const bool lead = blk ? threadIdx.x < 32 : true;  // one warp finishes the mover
     if (lead) {
+        const bool stay = cu > sh_upmax[tv / g.Lg];
         if (lane_id() == 0) {
             g.up[v] = cu;
             g.upstar[v] = cs;
             g.level[v] = tv | flr;  // still flagged: readers of this phase take dlv
+            if (low < kInf) atomicMax(&g.ctl->jlow_c[p], kInf - low);
+            if (tv != l + 1) atomicAdd(&g.ctl->jnonunit[p], 1);
+            if (stay) {
+                atomicAdd(&g.ctl->jstay[p], 1);
+                atomicMax(&g.ctl->jminup_c[p], kInf - cu);
+                atomicAdd(&g.ctl->jsdeg[p], (unsigned long long)dg);
+            }
         }
-        jump_push(g, p, lane_id() == 0 && cu > sh_upmax[tv / g.Lg], v, tv);
+        jump_push(g, pl, p, lane_id() == 0 && stay, v, tv, tv != l + 1);
     }
     return dg;
 }
@@ -2186,6 +2231,8 @@ __device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_up
                                 int32_t *sh_block) {
     const int lane = lane_id();
     const int32_t tc = g.ctl->tcount;
+    int32_t *bmin = sh_block + kWarpHist + 16;  // block's lowest carried level
+    if (threadIdx.x == 0) bmin[0] = kInf;
     // every endpoint of the batch that violates now is pending on its level
     for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
         const int i = i0 + lane;
@@ -2197,22 +2244,68 @@ __device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_up
             lx = g.level[x];
             v_ = g.up[x] > sh_upmax[lx / g.Lg];
         }
-        jump_push(g, 0, v_, x, lx);
+        jump_push(g, 0, 0, v_, x, lx, true);
     }
     if (!T.sync()) return false;
     unsigned long long visits = 0;
+    unsigned aff = 0;    // neighbours whose counters a move changed
+    int pb = 0;          // the pending list in use (entries taken are marked in place)
+    int32_t lprev = -1;  // level of the previous round
     int r = 0;
     for (;; ++r) {
-        const int cur = r & 1, nxt = cur ^ 1;
+        const int cur = r & 1, nxt = cur ^ 1;  // slots of this round's and the next round's totals
         const int32_t nc = g.ctl->jnext_c[cur];
         if (nc == 0) break;
-        const int32_t l = kInf - nc;
+        int32_t l = kInf - nc;
+        // Pure rounds (as for Algorithm 2's rounds): when every mover of the previous
+        // round (level x) went to x + 1 and still violates there, nothing else is
+        // pending on x + 1, and no neighbour of theirs outside them sits on x + 1 ..
+        // x + j + 2, each of the next j rounds moves the same set up one level (its
+        // members' targets stay at the next level: their count above it is their
+        // outside neighbours, all higher, within the cutoff that already held) and
+        // changes nothing else, while no other entry is pending on those levels and the
+        // cutoff stays below their smallest up-degree.  Those rounds are counted, not run.
+        int32_t skip = 0;
+        if (r > 0 && l == lprev + 1) {
+            const int32_t mprev_n = g.ctl->jmov[(r + 2) % 3];
+            if (g.ctl->jstay[cur] == mprev_n && g.ctl->jnonunit[cur] == 0) {
+                const int32_t oc = g.ctl->jother_c[cur], lc = g.ctl->jlow_c[cur];
+                const int64_t other = oc ? (int64_t)(kInf - oc) : (int64_t)kInf;
+                const int64_t low = lc ? (int64_t)(kInf - lc) : (int64_t)kInf;
+                const int32_t minup = kInf - g.ctl->jminup_c[cur];
+                int gg = l / g.Lg;
+                while (gg + 1 < g.G && sh_upmax[gg + 1] < minup) ++gg;
+                const int64_t top = (int64_t)(gg + 1) * g.Lg - 1;
+                const int64_t x = lprev;
+                const int64_t j = min(min(low - x - 3, other - x - 1), top - x - 1);
+                if (j >= 1) {
+                    skip = (int32_t)j;
+                    if (T.leader()) {
+                        const unsigned long long jm = (unsigned long long)j * (unsigned long long)mprev_n;
+                        const unsigned long long jv = (unsigned long long)j * g.ctl->jsdeg[cur];
+                        atomicAdd(&g.ctl->st[kStRounds], (unsigned long long)j);
+                        atomicAdd(&g.ctl->st[kStMoves], jm);
+                        atomicAdd(&g.ctl->st[kStVisits], jv);
+                        atomicAdd(&g.ctl->st[kStSkipRounds], (unsigned long long)j);
+                        atomicAdd(&g.ctl->st[kStSkipMoves], jm);
+                        atomicAdd(&g.ctl->st[kStSkipVisits], jv);
+                    }
+                    l += skip;
+                }
+            }
+        }
+        lprev = l;
         if (l >= g.K - 1 || r > g.K + 4) {  // the top group is never violated
             if (T.leader()) report(g, kErrInternal, 21, l, r, 0);
             return false;
         }
         const int32_t flr = round_flag(r), flp = round_flag(r + 1);
         const int mi = r % 3, mprev = (r + 2) % 3;
+        const uint64_t t_round = (g.trace && T.leader()) ? global_ns() : 0;
+        // the list is rewritten (live entries only) once most of it has been taken
+        const int32_t pc = g.ctl->jpend[pb], taken = g.ctl->jcons[pb];
+        const bool compact = 2 * taken > pc || pc > g.n;
+        const int pd = compact ? pb ^ 1 : pb;  // where this round's new entries go
         // phase A
         if (T.leader()) {
             g.ctl->jmov[(r + 1) % 3] = 0;  // last read in phase B of round r - 1
@@ -2222,59 +2315,91 @@ __device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_up
             const int32_t pm = g.ctl->jmov[mprev];
             for (int i = T.tid(); i < pm; i += T.nthreads()) atomicAnd(&g.level[g.TL[mprev][i].x], ~flp);
         }
-        const int32_t pc = g.ctl->jpend[cur];
+        int32_t cmin = kInf;  // lowest carried level
         for (int i0 = T.wid() * 32; i0 < pc; i0 += T.nwarps() * 32) {
             const int i = i0 + lane;
-            const int4 e = i < pc ? g.P[cur][i] : make_int4(0, kInf, 0, 0);
-            const bool mv = i < pc && e.y == l;
-            const bool carry = i < pc && e.y != l;
+            const int4 e = i < pc ? g.P[pb][i] : make_int4(0, -1, 0, 0);
+            const bool live = e.y >= 0;
+            const bool mv = live && (e.y == l || (skip && e.y == l - skip));
+            const bool carry = live && !mv;
             int32_t c = 0;
             if (mv) {
-                if ((g.level[e.x] & kLevelMask) != l) report(g, kErrInternal, 22, e.x, g.level[e.x], l);
+                if ((g.level[e.x] & kLevelMask) != e.y) report(g, kErrInternal, 22, e.x, g.level[e.x], e.y);
+                if (e.y != l) atomicAdd(&g.level[e.x], l - e.y);  // the skipped rounds' moves
                 atomicOr(&g.level[e.x], flr);
                 c = g.cap[e.x];
+                if (!compact) g.P[pb][i].y = -1;  // taken
+            }
+            if (!compact) {
+                if (carry) cmin = min(cmin, e.y);  // never a mover of this round staying on
+            } else {
+                jump_push(g, pd, nxt, carry, e.x, e.y, true);
             }
             const bool big = mv && c > g.block_cap;
             const int pos = warp_append(&g.ctl->jmov[mi], mv);
             if (mv) g.TL[mi][pos] = make_int4(e.x, c, 0, 0);
-            const int pb = warp_append(&g.ctl->jbig[cur], big);
-            if (big) g.M[0][pb] = make_int4(e.x, c, 0, 0);
-            jump_push(g, nxt, carry, e.x, e.y);
-            unsigned sm = __ballot_sync(kFull, mv && !big);
-            while (sm) {  // the warp computes the targets of its small movers
-                const int src = __ffs(sm) - 1;
-                sm &= sm - 1;
-                const int32_t v = __shfl_sync(kFull, e.x, src);
-                const int32_t t = jump_target<false>(g, v, l, sh_upmax, whist, nullptr);
-                if (lane == 0) g.dlv[v] = t;
+            const int pbg = warp_append(&g.ctl->jbig[cur], big);
+            if (big) g.M[0][pbg] = make_int4(e.x, c, 0, 0);
+        }
+        if (!compact) {  // the carried entries' lowest level, once per block
+            cmin = (int32_t)__reduce_min_sync(kFull, (unsigned)cmin);
+            if (lane == 0 && cmin < kInf) atomicMin(&bmin[0], cmin);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (bmin[0] < kInf) {
+                    atomicMax(&g.ctl->jnext_c[nxt], kInf - bmin[0]);
+                    atomicMax(&g.ctl->jother_c[nxt], kInf - bmin[0]);
+                }
+                bmin[0] = kInf;
             }
         }
         if (!T.sync()) return false;
-        // big tables: a block each (their targets are needed before phase B)
+        const uint64_t t_a = (g.trace && T.leader()) ? global_ns() : 0;
+        // the movers' targets: one warp per mover (a round's movers sit together in
+        // the list, so the warps that found them would take them one after another),
+        // a block per large table
+        const int32_t mc = g.ctl->jmov[mi];
         const int32_t nb = g.ctl->jbig[cur];
+        for (int i = T.wid(); i < mc; i += T.nwarps()) {
+            const int4 it = g.TL[mi][i];
+            if (it.y > g.block_cap) continue;
+            const int32_t t = jump_target<false>(g, it.x, l, sh_upmax, whist, nullptr);
+            if (lane == 0) g.dlv[it.x] = t;
+        }
         for (int b = T.bid(); b < nb; b += T.nthreads() / blockDim.x) {
             const int32_t v = g.M[0][b].x;
             const int32_t t = jump_target<true>(g, v, l, sh_upmax, sh_block, sh_block + kWarpHist);
             if (threadIdx.x == 0) g.dlv[v] = t;
         }
-        if (nb > 0 && !T.sync()) return false;
+        if (!T.sync()) return false;
         // phase B
-        const int32_t mc = g.ctl->jmov[mi];
         if (T.leader()) {
             atomicAdd(&g.ctl->st[kStRounds], 1ull);
             atomicAdd(&g.ctl->st[kStMoves], (unsigned long long)mc);
-            g.ctl->jpend[cur] = 0;  // read in phase A; filled again in round r + 1
-            g.ctl->jnext_c[cur] = 0;
+            // (every block read the list's counts at the start of the round, before phase A)
+            if (compact) {  // the old list was read in phase A; it is the next compaction's target
+                g.ctl->jpend[pb] = 0;
+                g.ctl->jcons[pb] = 0;
+            } else {
+                g.ctl->jcons[pb] += mc;  // the entries taken in phase A are this round's movers
+            }
+            g.ctl->jnext_c[cur] = 0;  // read at the start of this round
+            g.ctl->jstay[cur] = 0;
+            g.ctl->jnonunit[cur] = 0;
+            g.ctl->jother_c[cur] = 0;
+            g.ctl->jlow_c[cur] = 0;
+            g.ctl->jminup_c[cur] = 0;
+            g.ctl->jsdeg[cur] = 0;
         }
         for (int i = T.wid(); i < mc; i += T.nwarps()) {
             const int4 it = g.TL[mi][i];
             if (it.y > g.block_cap) continue;
-            const int32_t dg = jump_apply<false>(g, it.x, l, g.dlv[it.x], flr, nxt, sh_upmax, nullptr);
+            const int32_t dg = jump_apply<false>(g, it.x, l, g.dlv[it.x], flr, pd, nxt, sh_upmax, nullptr, &aff);
             if (lane == 0) visits += dg;
         }
         for (int b = T.bid(); b < nb; b += T.nthreads() / blockDim.x) {
             const int32_t v = g.M[0][b].x;
-            const int32_t dg = jump_apply<true>(g, v, l, g.dlv[v], flr, nxt, sh_upmax, sh_block + kWarpHist);
+            const int32_t dg = jump_apply<true>(g, v, l, g.dlv[v], flr, pd, nxt, sh_upmax, sh_block + kWarpHist, &aff);
             if (threadIdx.x == 0) visits += dg;
         }
         if (r > 0) {  // the previous round's movers that do not move now: target dropped
@@ -2285,6 +2410,15 @@ __device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_up
             }
         }
         if (!T.sync()) return false;
+        if (g.trace && T.leader() && g.ctl->trace_n < g.trace_cap) {
+            int32_t *rec = g.trace + 12 * g.ctl->trace_n++;
+            rec[0] = l; rec[1] = 2; rec[2] = mc; rec[3] = nb; rec[4] = pc - taken;
+            rec[5] = (int32_t)(global_ns() - t_round); rec[6] = (int32_t)(t_a - t_round); rec[7] = skip;
+            rec[8] = g.ctl->jstay[nxt]; rec[9] = g.ctl->jnonunit[nxt];
+            rec[10] = g.ctl->jother_c[nxt] ? kInf - g.ctl->jother_c[nxt] : -1;
+            rec[11] = g.ctl->jlow_c[nxt] ? kInf - g.ctl->jlow_c[nxt] : -1;
+        }
+        pb = pd;
     }
     // the last round's movers lose their flag and their target (dlv back to -1)
     if (r > 0) {
@@ -2297,7 +2431,9 @@ __device__ bool ins_rounds_jump(Team &T, const GraphCtx &g, const int32_t *sh_up
         }
     }
     visits = warp_sum64(visits);
+    const unsigned long long affs = warp_sum64(aff);
     if (lane == 0 && visits) atomicAdd(&g.ctl->st[kStVisits], visits);
+    if (lane == 0 && affs) atomicAdd(&g.ctl->st[kStAffected], affs);
     if (!T.sync()) return false;
     return true;
 }

@@ -29,7 +29,8 @@ enum : int32_t {
 // statistics slots (Ctl::st)
 enum : int {
     kStSubmitted = 0, kStSelfLoops, kStDuplicates, kStFiltered, kStValid, kStRounds, kStMoves,
-    kStVisits, kStDlEvals, kStDlVisits, kStSlotsScanned, kStUpVisits, kStCount
+    kStVisits, kStDlEvals, kStDlVisits, kStSlotsScanned, kStUpVisits, kStAffected,
+    kStSkipRounds, kStSkipMoves, kStSkipVisits, kStSkipUpVisits, kStCount
 };
 
 enum : int32_t { kOpInsert = 0, kOpDelete = 1 };
@@ -56,13 +57,25 @@ struct Ctl {
     int32_t ilow_c[3];
     unsigned long long isdeg[3];
     unsigned long long isup[3];
-    // insertion, jump variant: pending violators in P[i] (round parity) and kInf
-    // minus their lowest level (0: none); movers of a round (index mod 3, in TL)
-    // and those with large tables (round parity, in M[0])
+    // insertion, jump variant: pending violators in P[i] (the list in use) and,
+    // per round parity, kInf minus their lowest level (0: none); movers of a round
+    // (index mod 3, in TL) and those with large tables (round parity, in M[0])
     int32_t jpend[2];
+    int32_t jcons[2];     // jump variant: entries of P[i] already taken (marked in place)
     int32_t jnext_c[2];
     int32_t jmov[3];
     int32_t jbig[2];
+    // jump variant, per round parity, for skipping pure rounds: movers still
+    // violating at their target; movers whose target is not l + 1; kInf minus the
+    // lowest level of a pending entry that is not such a mover, of a neighbour of a
+    // mover that is no mover (>= l + 1), and of the staying movers' up-degree; the
+    // staying movers' degree sum
+    int32_t jstay[2];
+    int32_t jnonunit[2];
+    int32_t jother_c[2];
+    int32_t jlow_c[2];
+    int32_t jminup_c[2];
+    unsigned long long jsdeg[2];
     int32_t mcnt[2];      // table growth / deletion movers
     int32_t tlcnt[2];     // thread-mode movers
     int32_t clcnt[2];     // chunk items

@@ -30,7 +30,13 @@ def test_reference_line_matches_native_config():
         scale, batch = 12, 4096
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
-    assert d["config"] == bench.plain_config(A, 1 << 12, d["config"]["m"], 1)
+    # the config names the batch the oracle actually ran (1024), not the native arm's
+    want = bench.plain_config(A, 1 << 12, d["config"]["m"], 1, batch=1024)
+    cfg = dict(d["config"])
+    assert cfg.pop("native_arm_batch") == 4096
+    cfg.pop("stream")
+    want.pop("stream")
+    assert cfg == want and cfg["batch"] == 1024 and "B1e3" in cfg["workload"]
     assert d["config"]["m"] > 0 and d["steps"] == 3 and d["warmup"] == 3
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] > 0 and cb["sample"]

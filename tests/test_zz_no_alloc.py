@@ -67,3 +67,81 @@ def test_static_rejects_oversized_batches(P):
     assert _static(P, g, big, 0) == P.PLDS_EINVAL
     assert _static(P, g, big[:10], 2) == P.PLDS_EINVAL
     g.close()
+
+
+def _counting_handle(P, n):
+    """A handle whose device memory comes from a counting allocator callback."""
+    L = P.load()
+    calls = {"alloc": 0, "free": 0}
+
+    def _alloc(nbytes, stream, ctx):
+        calls["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+
+    def _free(ptr, nbytes, stream, ctx):
+        calls["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    alloc = P.PldsAllocator(P.ALLOC_FN(_alloc), P.FREE_FN(_free), None)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = L.plds_create_ex(n, 0.4, 3.0, 0, ctypes.byref(alloc), stream, 0)
+    assert h
+    return P.PLDS(n, _borrowed=h), h, calls, alloc
+
+
+def test_static_calls_make_no_allocation(P):
+    """Every device buffer the handle owns comes from the caller's allocator; the
+    static calls (insertions and deletions, host and device edges) call it zero
+    times, and their results equal the regular calls'."""
+    n = 5000
+    e = W.chung_lu(n, 30_000, 2.3, seed=23)
+    g, h, calls, _keep = _counting_handle(P, n)
+    ref = P.PLDS(n)
+    before = dict(calls)
+    ins = W.shuffled(e, 7)
+    for batch in (ins[:12_000], ins[12_000:24_000]):
+        ref.insert(batch)
+        assert _static(P, g, batch, 0) == P.PLDS_OK
+    dev = torch.from_numpy(W.shuffled(e, 8)[:9_000]).cuda()  # edges already on the device
+    ref.delete(dev)
+    rc = P.load().plds_batch_static(h, ctypes.c_void_p(dev.data_ptr()), dev.shape[0], 1)
+    assert rc == P.PLDS_OK
+    assert calls == before, f"static calls allocated: {calls} vs {before}"
+    assert np.array_equal(g.levels(), ref.levels())
+    d, u, s = g.counters()
+    rd, ru, rs = ref.counters()
+    assert np.array_equal(d, rd) and np.array_equal(u, ru) and np.array_equal(s, rs)
+    P.load().plds_destroy(h)
+    ref.close()
+
+
+def test_static_full_pool_reports_enomem_unchanged(P):
+    """A batch whose tables do not fit the adjacency pool: PLDS_ENOMEM with levels and
+    counters as before the call (growing the pool would allocate); a regular call
+    with the same batch then grows the pool and gives the oracle's result."""
+    from oracle import oracle as O
+    n = 2000
+    e = W.erdos_renyi(n, 400_000, seed=31)  # ~8 * 400k slots of tables: more than the initial pool
+    g, h, calls, _keep = _counting_handle(P, n)
+    o = O.OraclePLDS(n)
+    hit = False
+    for s0 in range(0, e.shape[0], 50_000):
+        b = np.ascontiguousarray(e[s0:s0 + 50_000])
+        lv, cn = g.levels().copy(), [x.copy() for x in g.counters()]
+        before = dict(calls)
+        rc = _static(P, g, b, 0)
+        assert calls == before
+        if rc == P.PLDS_ENOMEM:
+            hit = True
+            assert np.array_equal(g.levels(), lv)
+            for x, y in zip(g.counters(), cn):
+                assert np.array_equal(x, y)
+            g.insert(b)  # the regular call grows the pool
+        else:
+            assert rc == P.PLDS_OK
+        assert o.insert(b) == 0
+        assert np.array_equal(g.levels(), o.levels())
+        if hit:
+            break
+    assert hit, "the pool never filled"
+    P.load().plds_destroy(h)
