@@ -51,8 +51,9 @@ UNIT = "updates/s"
 # dram bytes / executed algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": None, "dram_per_algo_byte": None,
-               "capture": "ncu DRAM counters of three k_batch_grid launches of the R-MAT 20 step stream"}
+NCU_TRAFFIC = {"kernel_sha": "7c622e60a125de01", "dram_per_algo_byte": 1.0005,
+               "capture": "ncu DRAM counters of three k_batch_grid launches of the R-MAT 20 step stream "
+                          "(profiles/k_batch_grid_traffic_rmat20_B1e6.md)"}
 
 
 def kernel_sha() -> str:
