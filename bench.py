@@ -664,7 +664,8 @@ def run_batched(args):
     pre_r = [pre[i] for i in mine]
     rnds_r = [[r[i] for i in mine] for r in rnds]
     res = batched_results(P, ns_r, pre_r, rnds_r, args.warmup, args.tune_trials, args.plain_rounds,
-                          autotune=not args.no_autotune, cpu_every=16 if world == 1 else 0, local=local)
+                          autotune=not args.no_autotune, cpu_every=4 if world == 1 else 0, cpu_rounds=args.rounds,
+                          local=local)
     w = res["warmup_rounds"]
     upd = sum(sum(i.shape[0] + d.shape[0] for i, d in rnds_r[r]) for r in range(w, args.rounds))
     secs = upd / res["updates_per_s"]
@@ -717,10 +718,10 @@ def make_serving_stream(e: np.ndarray, requests: int, seed: int = 5):
     return np.ascontiguousarray(pre), reqs
 
 
-def serving_cpu_baseline(n: int, reqs, budget: int = 200_000) -> dict:
-    """The oracle (1 core) on the stream's first requests until `budget` updates,
-    applied to an empty graph of the same n (building the preloaded 90 % state
-    would take the oracle over ten minutes)."""
+def serving_cpu_baseline(n: int, reqs, budget: int = 1_000_000, min_requests: int = 40) -> dict:
+    """The oracle (1 core) on the stream's first requests (at least `min_requests`,
+    until `budget` updates), applied to an empty graph of the same n (building the
+    preloaded 90 % state would take the oracle over ten minutes)."""
     from oracle import oracle as O
     o = O.OraclePLDS(n)
     upd, k = 0, 0
@@ -734,7 +735,7 @@ def serving_cpu_baseline(n: int, reqs, budget: int = 200_000) -> dict:
             o.delete(b)
         k += 1
         upd += 0 if b is None else b.shape[0]
-        if upd >= budget:
+        if upd >= budget and k >= min_requests:
             break
     dt = time.perf_counter() - t0
     return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
@@ -1052,7 +1053,8 @@ def main():
                                             cpu=not args.no_cpu_baseline)}
         ns_b, pre_b, rnds_b = make_batched(args.graphs, args.rounds)
         forms["batched"] = batched_results(P, ns_b, pre_b, rnds_b, 3, min(args.tune_trials, 8), args.plain_rounds,
-                                           cpu_every=0 if args.no_cpu_baseline else 16, local=local)
+                                           cpu_every=0 if args.no_cpu_baseline else 4, cpu_rounds=args.rounds,
+                                           local=local)
 
     phases = {}
     for kind in ("ins", "del"):
