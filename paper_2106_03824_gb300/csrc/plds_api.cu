@@ -145,7 +145,7 @@ struct plds {
     int64_t launches = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // persistent state
-    DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, inc;
+    DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, dslack, inc;
     DevBuf pool, pool_top, ctl;
     int64_t pool_cap = 0;
     int64_t pool_live = 0;   // slots in use after the last compaction
@@ -227,7 +227,7 @@ static int64_t pow2_at_least(int64_t x) {
 
 static void free_all(plds *h) {
     DevBuf *bufs[] = {&h->upmax, &h->dnmin, &h->powtab, &h->level, &h->deg,   &h->up,    &h->upstar,
-                      &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->inc,   &h->pool,
+                      &h->off,   &h->cap,   &h->tomb,   &h->stamp, &h->dlv,   &h->dslack, &h->inc,   &h->pool,
                       &h->pool_top, &h->ctl, &h->acc,   &h->M[0],  &h->M[1],  &h->TL[0], &h->TL[1], &h->TL[2],
                       &h->P[0],  &h->P[1],  &h->R, &h->R2,     &h->bins,  &h->levlist, &h->CL[0], &h->CL[1],
                       &h->CL[2], &h->edges, &h->hset,   &h->ukeys, &h->vkeys, &h->touched, &h->S, &h->arena, &h->trace,
@@ -388,6 +388,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.tomb = P<int32_t>(h->tomb);
     g.stamp = P<int32_t>(h->stamp);
     g.dlv = P<int32_t>(h->dlv);
+    g.dslack = P<int32_t>(h->dslack);
     g.inc = P<int32_t>(h->inc);
     g.slots = P<int32_t>(h->pool);
     g.pool_top = P<unsigned long long>(h->pool_top);
@@ -599,6 +600,7 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
               dev_get(h, h->level, 4 * N) && dev_get(h, h->deg, 4 * N) && dev_get(h, h->up, 4 * N) &&
               dev_get(h, h->upstar, 4 * N) && dev_get(h, h->off, 8 * N) && dev_get(h, h->cap, 4 * N) &&
               dev_get(h, h->tomb, 4 * N) && dev_get(h, h->stamp, 4 * N) && dev_get(h, h->dlv, 4 * N) &&
+              dev_get(h, h->dslack, 4 * N) &&
               dev_get(h, h->inc, 4 * N) && dev_get(h, h->pool, 4 * (size_t)h->pool_cap) &&
               dev_get(h, h->pool_top, 8) && dev_get(h, h->ctl, sizeof(Ctl)) && dev_get(h, h->acc, 8 * N) &&
               dev_get(h, h->lout, 4 * N) && dev_get(h, h->lfill[0], 4 * N) && dev_get(h, h->lfill[1], 4 * N) &&

@@ -1564,8 +1564,10 @@ __device__ __forceinline__ int warp_best_group(const int32_t *hist, int G, int g
     return (int)__reduce_max_sync(kFull, (unsigned)(best + 1)) - 1;
 }
 
-// Largest x in [lo, hi] with above + sum_{y=x..hi} h[y-lo] >= need, or -1.  One warp.
-__device__ __forceinline__ int warp_window_find(const int32_t *h, int lo, int hi, int above, int need) {
+// Largest x in [lo, hi] with above + sum_{y=x..hi} h[y-lo] >= need, or -1; *cnt gets
+// that sum at x (the neighbours on x or above).  One warp.
+__device__ __forceinline__ int warp_window_find(const int32_t *h, int lo, int hi, int above, int need,
+                                                int *cnt) {
     const int lane = lane_id();
     const int top = hi - lo;  // lane L covers offsets top-8L .. top-8L-7 (highest levels first)
     int local = 0;
@@ -1575,15 +1577,19 @@ __device__ __forceinline__ int warp_window_find(const int32_t *h, int lo, int hi
     }
     int tot;
     int run = above + warp_exclusive(local, &tot);
-    int found = -1;
+    int found = -1, fcnt = 0;
     for (int b = 0; b < 8; ++b) {
         const int idx = top - 8 * lane - b;
         if (idx >= 0 && found < 0) {
             run += h[idx];
-            if (run >= need) found = lo + idx;
+            if (run >= need) {
+                found = lo + idx;
+                fcnt = run;
+            }
         }
     }
     const unsigned m = __ballot_sync(kFull, found >= 0);
+    *cnt = m ? __shfl_sync(kFull, fcnt, __ffs(m) - 1) : 0;
     return m ? __shfl_sync(kFull, found, __ffs(m) - 1) : -1;
 }
 
@@ -1620,9 +1626,13 @@ __device__ __forceinline__ int warp_range_sum(const int32_t *h, int lo, int hi) 
 // has at least dnmin[gn(l'-1)] neighbours on it or above, found from a histogram of
 // the neighbours' groups and then of the levels in the best group.  The first scan
 // also counts the 256 levels just below lw - 1 one by one: when the best group lies
-// in that window (the common case) no second scan is needed.
+// in that window (the common case) no second scan is needed.  *slack gets, for an
+// answer d > 0, the neighbours on d - 1 or above minus dnmin[gn(d - 1)] (>= 0; kInf
+// for d = 0, 0 where it is not counted): while later moves do not take it below 0,
+// the answer stays d.
 __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
-                                     int32_t *hist) {
+                                     int32_t *hist, int32_t *slack) {
+    *slack = kInf;
     if (lw < 2) return 0;
     const int lane = lane_id();
     const int32_t Lg = g.Lg, G = g.G;
@@ -1651,9 +1661,12 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
     if (best < 0) return 0;
     const int32_t need = sh_dnmin[best], a = best * Lg;
     int32_t hi = min((best + 1) * Lg - 1, xmax);
+    int cnt = 0;
+    *slack = 0;
     if (one && a >= w0) {  // the best group's levels were counted by the first scan
         const int above = win[kWindow] + warp_range_sum(win, hi + 1 - w0, xmax - w0);
-        const int found = warp_window_find(win + (a - w0), a, hi, above, need);
+        const int found = warp_window_find(win + (a - w0), a, hi, above, need, &cnt);
+        if (found >= 0) *slack = cnt - need;
         return found >= 0 ? found + 1 : a + 1;  // a + 1 unreachable: cnt(a) >= need holds
     }
     for (;;) {
@@ -1666,16 +1679,20 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
             else if (x >= lo) atomicAdd(&hist[x - lo], 1);
         });
         __syncwarp();
-        const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
+        const int found = warp_window_find(hist, lo, hi, hist[kWindow], need, &cnt);
         __syncwarp();
-        if (found >= 0) return found + 1;
+        if (found >= 0) {
+            *slack = cnt - need;
+            return found + 1;
+        }
         if (lo == a) return a + 1;  // unreachable: cnt(a) >= need holds
         hi = lo - 1;
     }
 }
 
 __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, const int32_t *sh_dnmin,
-                                      int32_t *hist, int32_t *res) {
+                                      int32_t *hist, int32_t *res, int32_t *slack) {
+    *slack = kInf;  // as in warp_desire_level
     if (lw < 2) return 0;
     const int32_t Lg = g.Lg, G = g.G;
     const int32_t ng = g.cap[w] >> 2;
@@ -1708,14 +1725,20 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     if (best < 0) return 0;
     const int32_t need = sh_dnmin[best], a = best * Lg;
     int32_t hi = min((best + 1) * Lg - 1, xmax);
+    *slack = 0;
     if (one && a >= w0) {  // the best group's levels were counted by the first scan
         if (threadIdx.x < 32) {
+            int cnt = 0;
             const int above = win[kWindow] + warp_range_sum(win, hi + 1 - w0, xmax - w0);
-            const int found = warp_window_find(win + (a - w0), a, hi, above, need);
-            if (threadIdx.x == 0) *res = found;
+            const int found = warp_window_find(win + (a - w0), a, hi, above, need, &cnt);
+            if (threadIdx.x == 0) {
+                res[0] = found;
+                res[1] = cnt;
+            }
         }
         __syncthreads();
-        const int found = *res;
+        const int found = res[0];
+        if (found >= 0) *slack = res[1] - need;
         __syncthreads();
         return found >= 0 ? found + 1 : a + 1;  // a + 1 unreachable: cnt(a) >= need holds
     }
@@ -1729,13 +1752,21 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
         });
         __syncthreads();
         if (threadIdx.x < 32) {
-            const int found = warp_window_find(hist, lo, hi, hist[kWindow], need);
-            if (threadIdx.x == 0) *res = found;
+            int cnt = 0;
+            const int found = warp_window_find(hist, lo, hi, hist[kWindow], need, &cnt);
+            if (threadIdx.x == 0) {
+                res[0] = found;
+                res[1] = cnt;
+            }
         }
         __syncthreads();
-        const int found = *res;
+        const int found = res[0];
+        const int cntf = res[1];
         __syncthreads();
-        if (found >= 0) return found + 1;
+        if (found >= 0) {
+            *slack = cntf - need;
+            return found + 1;
+        }
         if (lo == a) return a + 1;  // unreachable: cnt(a) >= need holds
         hi = lo - 1;
     }
@@ -1746,7 +1777,10 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
 // classify into a warp list (small tables, from the front of RL) and a block list
 // (large tables, from the back), then compute.  A result d becomes a pending
 // entry in P[q] unless it equals the vertex's current pending level; results at
-// or below lmin contradict the level lemma and are reported.
+// or below lmin contradict the level lemma and are reported.  A pending vertex
+// whose slack has not gone below 0 since its last evaluation would get the same
+// answer again: that evaluation is counted (as the oracle counts it) without the
+// scan.
 template <class Team>
 __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t count, int q, int32_t lmin,
                          const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist, unsigned long long &evals,
@@ -1759,9 +1793,14 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
         int32_t w = 0;
         if (i < count) {
             w = src[i];
-            const int32_t lw = g.level[w], us = g.upstar[w], c = g.cap[w];
+            const int32_t lw = g.level[w], us = g.upstar[w], c = g.cap[w], dv = g.dlv[w];
             viol = lw > 0 && us < sh_dnmin[(lw - 1) / g.Lg];
             big = c > g.block_cap;
+            if (viol && dv >= 0 && g.dslack[w] >= 0) {  // same answer as last time: counted only
+                viol = false;
+                evals++;
+                evisits += g.deg[w];
+            }
         }
         const int pw = warp_append(&g.ctl->rcnt[1], viol && !big);
         if (viol && !big) RL[pw] = w;
@@ -1772,8 +1811,10 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
     const int32_t nw = g.ctl->rcnt[1], nb = g.ctl->rbcnt;
     for (int i = T.wid(); i < nw; i += T.nwarps()) {
         const int32_t w = RL[i], lw = g.level[w];
-        const int32_t d = warp_desire_level(g, w, lw, sh_dnmin, whist);
+        int32_t sl;
+        const int32_t d = warp_desire_level(g, w, lw, sh_dnmin, whist, &sl);
         if (lane == 0) {
+            g.dslack[w] = sl;
             evals++;
             evisits += g.deg[w];
             if (d <= lmin) {
@@ -1788,8 +1829,10 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
     }
     for (int i = T.bid(); i < nb; i += (T.nthreads() / blockDim.x)) {
         const int32_t w = RL[g.n - 1 - i], lw = g.level[w];
-        const int32_t d = block_desire_level(g, w, lw, sh_dnmin, bhist, bhist + kWarpHist);
+        int32_t sl;
+        const int32_t d = block_desire_level(g, w, lw, sh_dnmin, bhist, bhist + kWarpHist, &sl);
         if (threadIdx.x == 0) {
+            g.dslack[w] = sl;
             evals++;
             evisits += g.deg[w];
             if (d <= lmin) {
@@ -1825,6 +1868,14 @@ __device__ __forceinline__ int del_effect(const GraphCtx &g, int32_t w, int32_t 
     aff += lw <= pv + 1;  // w lost an up- or up*-neighbour
     if (lw < l + 2) return 0;
     return lw - 1 <= pv ? 1 : 2;
+}
+
+// A mover (pv -> l) next to a pending vertex w whose desire-level is dv: the count
+// behind w's answer (neighbours on dv - 1 or above) loses the mover when
+// l < dv - 1 <= pv, and the slack of that answer with it.
+__device__ __forceinline__ void del_slack(const GraphCtx &g, int32_t w, int32_t dv, int32_t l, int32_t pv) {
+    const int32_t xs = dv - 1;
+    if (l < xs && xs <= pv) atomicSub(&g.dslack[w], 1);
 }
 
 template <class Team>
@@ -1937,7 +1988,13 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
                 }
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if ((maybe >> k & 1u) && g.dlv[ws[k]] >= 0) push |= 1u << k;
+                    if ((push | maybe) >> k & 1u) {
+                        const int32_t dv = g.dlv[ws[k]];
+                        if (dv >= 0) {
+                            push |= 1u << k;  // pending: rechecked
+                            del_slack(g, ws[k], dv, l, it.w);
+                        }
+                    }
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if ((push >> k & 1u) && atomicExch(&g.stamp[ws[k]], sid) == sid) push &= ~(1u << k);
@@ -1976,7 +2033,13 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
             }
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                if ((maybe >> k & 1u) && g.dlv[ws[k]] >= 0) push |= 1u << k;
+                if ((push | maybe) >> k & 1u) {
+                    const int32_t dv = g.dlv[ws[k]];
+                    if (dv >= 0) {
+                        push |= 1u << k;  // pending: rechecked
+                        del_slack(g, ws[k], dv, l, it[k >> 2].w);
+                    }
+                }
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 if ((push >> k & 1u) && atomicExch(&g.stamp[ws[k]], sid) == sid) push &= ~(1u << k);

@@ -111,6 +111,7 @@ struct GraphCtx {
     int32_t *tomb;         // [n] tombstones in the table
     int32_t *stamp;        // [n] dedupe stamps
     int32_t *dlv;          // [n] pending desire-level, -1 when none
+    int32_t *dslack;       // [n] deletion: slack of a pending vertex's desire-level (see dl_batch)
     int32_t *inc;          // [n] incoming insertions of the batch
     int32_t *slots;        // adjacency pool
     unsigned long long *pool_top;  // slots handed out
