@@ -1059,13 +1059,21 @@ __device__ __forceinline__ bool ins_finish_mover(const GraphCtx &g, int32_t v, i
     return again;
 }
 
-// A mover that climbs on: its new up-degree and degree go into the block's totals
-// (shared atomics; published once per block at the end of the phase).
-__device__ __forceinline__ void ff_note(const RoundStage &st, int32_t nu, int32_t deg) {
-    atomicAdd(&st.ff[0], 1);
-    atomicMin(&st.ff[1], nu);
-    atomicAdd(&st.ff64[0], (unsigned long long)deg);
-    atomicAdd(&st.ff64[1], (unsigned long long)nu);
+// The lanes' movers that climb on (again): their new up-degrees and degrees go
+// into the block's totals -- reduced over the warp first, then one lane's shared
+// atomics (published once per block at the end of the phase).  All lanes call.
+__device__ __forceinline__ void ff_note(const RoundStage &st, bool again, int32_t nu, int32_t deg) {
+    const unsigned m = __ballot_sync(kFull, again);
+    if (m == 0) return;
+    const int32_t mn = (int32_t)__reduce_min_sync(kFull, again ? (unsigned)nu : (unsigned)kInf);
+    const unsigned long long sd = warp_sum64(again ? (unsigned long long)deg : 0ull);
+    const unsigned long long su = warp_sum64(again ? (unsigned long long)nu : 0ull);
+    if (lane_id() == __ffs(m) - 1) {
+        atomicAdd(&st.ff[0], __popc(m));
+        atomicMin(&st.ff[1], mn);
+        atomicAdd(&st.ff64[0], sd);
+        atomicAdd(&st.ff64[1], su);
+    }
 }
 
 // Queue the table scans of the lanes' newly marked vertices (their first move of
@@ -1253,7 +1261,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 visits += ideg;
                 upv += up_v;
                 const bool again = have && ins_finish_mover(g, it.x, up_v, cnt_l, l, fcur, fnext, cut_next);
-                if (again) ff_note(st, up_v - cnt_l, ideg);
+                ff_note(st, again, up_v - cnt_l, ideg);
                 enqueue_ins(g, st, again, it.x, have ? 1 << it.y : 0, (int64_t)it.z * 4, -1, 0, 0, k + 1, wsm);
             }
             // chunk items: four per warp iteration, all loads of a step issued together;
@@ -1360,8 +1368,8 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     nul = upl - total;
                     cont = ins_finish_mover(g, mine.x, upl, total, l, fcur, fnext, cut_next);
                     for (int p = nul; cont && lol >= 0 && (p & 3); ++p) lwr[(int64_t)lol * 4 + p] = kEmpty;
-                    if (cont) ff_note(st, nul, dgl);
                 }
+                ff_note(st, cont, nul, dgl);
                 // a mover that keeps climbing is scanned next from its up-list, or from
                 // its table again when its list did not fit
                 int32_t mc_cap = 0;
