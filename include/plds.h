@@ -85,6 +85,9 @@ typedef struct plds_stats {
     int64_t skipped_moves;
     int64_t skipped_visits;
     int64_t skipped_up_visits;
+    int64_t pre_ns;        /* device time of the last call's steps before the level rounds
+                              (preprocessing, table growth/shrinking, adjacency and counter
+                              updates; part of kernel_ns) */
 } plds_stats_t;
 
 /* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */

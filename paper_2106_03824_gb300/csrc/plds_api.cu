@@ -35,10 +35,89 @@ static int set_status(int s) {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// The level rounds of one batch (after the step kernels below), one cooperative
+// launch: 152 blocks (one per SM) x 512 threads, grid barriers between rounds.
 __global__ void __launch_bounds__(512) k_batch_grid(const __grid_constant__ GraphCtx g) {
     extern __shared__ int32_t sh[];
     GridTeam T{g.ctl, g.wait_limit_ns, g.barrier_sleep_ns};
-    run_batch(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh, 0);
+    run_batch<GridTeam, true>(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh, 0);
+}
+
+// The steps before the level rounds (preprocessing, table growth and shrinking,
+// adjacency and counter updates) as plain kernels for the single-graph batch
+// calls: they need no grid barrier -- each kernel boundary orders one step against
+// the next -- so they run at full occupancy instead of one block per SM.  Each
+// starts by reading the error word: a step that failed (bad id, pool too small)
+// stops the rest, and the cooperative rounds kernel after them as well.
+constexpr int kPreThreads = 256;
+#define PRE_SCRATCH __shared__ unsigned long long sh_res[kPreThreads / 32 + 1]
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_canon(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    PRE_SCRATCH;
+    pre_canon(g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_filter(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    PRE_SCRATCH;
+    pre_filter(g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_grow_request(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    PRE_SCRATCH;
+    pre_grow_request(g, sh_res);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_pool_check(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_pool_check(g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_alloc(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    PRE_SCRATCH;
+    pre_alloc(g, sh_res);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_grow(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_grow(g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_apply_insert(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    FreeTeam T;
+    step_apply_insert(T, g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_apply_delete(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    FreeTeam T;
+    if (T.leader()) {
+        g.ctl->nextmin[0] = kInf;
+        g.ctl->nextmin[1] = kInf;
+    }
+    step_apply_delete(T, g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_plan(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    PRE_SCRATCH;
+    pre_shrink_plan(g, sh_res);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_small(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_shrink_small(g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_big(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    __shared__ int sh_scan[64];
+    FreeTeam T;
+    shrink_big(T, g, sh_scan);
 }
 
 // Coreness estimate (Definition "Coreness Estimate"): exponent
@@ -143,7 +222,7 @@ struct plds {
     int64_t pool_grows = 0;
     plds_stats_t last{};
     int64_t launches = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // batch start, end; end of the step kernels
     // persistent state
     DevBuf upmax, dnmin, powtab, level, deg, up, upstar, off, cap, tomb, stamp, dlv, dslack, inc;
     DevBuf pool, pool_top, ctl;
@@ -442,6 +521,38 @@ static void raise_smem_limit(K kernel, std::atomic<bool> (&done)[kAttrDevices], 
 
 static std::atomic<bool> g_attr_batch[kAttrDevices];
 
+// The step kernels of one batch attempt, in stream order, then pre_done set so
+// that the cooperative kernel starts at the rounds.  Records ev0 before them and
+// evm after them.
+static void launch_pre(plds *h, GraphCtx &g) {
+    const int blocks = std::max(1, h->num_sms * 8);
+    cudaStream_t s = h->stream;
+    cudaEventRecord(h->ev0, s);
+    int k = 0;
+    if (g.B > 0) {
+        k_pre_canon<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_filter<<<blocks, kPreThreads, 0, s>>>(g);
+        k += 2;
+    }
+    if (g.op == kOpInsert) {
+        k_pre_grow_request<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_pool_check<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_alloc<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_grow<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_apply_insert<<<blocks, kPreThreads, 0, s>>>(g);
+        k += 5;
+    } else {
+        k_pre_apply_delete<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_shrink_plan<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_shrink_small<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_shrink_big<<<blocks, kPreThreads, 0, s>>>(g);
+        k += 4;
+    }
+    cudaEventRecord(h->evm, s);
+    h->launches += k;
+    g.pre_done = 1;
+}
+
 static int launch_batch(plds *h, const GraphCtx &g) {
     const int threads = block_threads(h);
     const size_t smem = smem_bytes(threads);
@@ -452,7 +563,7 @@ static int launch_batch(plds *h, const GraphCtx &g) {
     if (per_sm < 1) return PLDS_EDEVICE;
     dim3 grid(h->num_sms * per_sm), block(threads);
     void *args[] = {(void *)&g};
-    cudaEventRecord(h->ev0, h->stream);
+    if (!g.pre_done) cudaEventRecord(h->ev0, h->stream);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_batch_grid, grid, block, args, smem, h->stream);
     cudaEventRecord(h->ev1, h->stream);
     h->launches++;
@@ -499,6 +610,7 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
         if (op == kOpInsert) cudaMemsetAsync(h->bins.p, 0, sizeof(int32_t) * ((size_t)h->T.K + 1), h->stream);
         GraphCtx g = make_ctx(h, op, dedges, B);
         h->stamp_base += h->T.K + 2;
+        launch_pre(h, g);
         int rc = launch_batch(h, g);
         if (rc) return rc;
         cudaMemcpyAsync(&h->host_ctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
@@ -509,6 +621,7 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
         }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last.kernel_ns += (int64_t)(ms * 1e6);
+        if (cudaEventElapsedTime(&ms, h->ev0, h->evm) == cudaSuccess) h->last.pre_ns += (int64_t)(ms * 1e6);
         cudaGetLastError();
         const Ctl &c = h->host_ctl;
         h->last.err_bits = c.err;
@@ -579,7 +692,8 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
         return nullptr;
     }
     cudaGetDevice(&h->device);
-    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaEventCreate(&h->evm) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         set_status(PLDS_EDEVICE);
@@ -1274,6 +1388,7 @@ void plds_destroy(plds_t *h) {
     cudaStreamSynchronize(h->stream);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->evm) cudaEventDestroy(h->evm);
     cudaGetLastError();
     delete h;
 }
@@ -1376,6 +1491,7 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     g.arena = reinterpret_cast<int32_t *>(base + kStOffArena);
     g.arena_cap = kStaticArena;
     h->stamp_base += h->T.K + 2;
+    launch_pre(h, g);
     int rc = launch_batch(h, g);
     if (rc) return set_status(rc);
     cudaMemcpyAsync(&h->host_ctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
@@ -1386,6 +1502,7 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
     }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last.kernel_ns = (int64_t)(ms * 1e6);
+    if (cudaEventElapsedTime(&ms, h->ev0, h->evm) == cudaSuccess) h->last.pre_ns = (int64_t)(ms * 1e6);
     cudaGetLastError();
     const Ctl &c = h->host_ctl;
     h->last.err_bits = c.err;

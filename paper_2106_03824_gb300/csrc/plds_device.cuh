@@ -117,6 +117,18 @@ struct BlockTeam {
     }
 };
 
+// A plain (non-cooperative) grid running one step that needs no team barrier:
+// the kernel boundary orders it against the next step.
+struct FreeTeam {
+    static constexpr bool kGrid = false;
+    __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ int nthreads() const { return gridDim.x * blockDim.x; }
+    __device__ int wid() const { return tid() >> 5; }
+    __device__ int nwarps() const { return nthreads() >> 5; }
+    __device__ int bid() const { return blockIdx.x; }
+    __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+};
+
 // ---------------------------------------------------------------------------
 // Warp helpers (all 32 lanes must call)
 // ---------------------------------------------------------------------------
@@ -506,11 +518,49 @@ __device__ void step_apply_delete(Team &T, const GraphCtx &g) {
     }
 }
 
+// Rebuild x's table (c slots, d live keys) in place as nc slots, through arena
+// room at base: one warp (all lanes call).
+__device__ __forceinline__ void shrink_table_warp(const GraphCtx &g, int32_t sx, int32_t snc, int32_t sc,
+                                                  int32_t sbase, int32_t sd) {
+    int64_t off = g.off[sx];
+    int4 *t4 = reinterpret_cast<int4 *>(g.slots + off);
+    int32_t *ar = g.arena + sbase;
+    int written = 0;
+    for (int j0 = 0; j0 < (sc >> 2); j0 += 32) {
+        int j = j0 + lane_id();
+        int4 q = j < (sc >> 2) ? t4[j] : empty4();
+        int cnt = (q.x >= 0) + (q.y >= 0) + (q.z >= 0) + (q.w >= 0);
+        int tot;
+        int ex = warp_exclusive(cnt, &tot);
+        int p = written + ex;
+        // the table holds exactly deg live keys; never write past the reservation
+        if (q.x >= 0 && p < sd) ar[p++] = q.x;
+        if (q.y >= 0 && p < sd) ar[p++] = q.y;
+        if (q.z >= 0 && p < sd) ar[p++] = q.z;
+        if (q.w >= 0 && p < sd) ar[p++] = q.w;
+        written += tot;
+    }
+    if (written != sd) {  // counters and table disagree: report, keep the table
+        if (lane_id() == 0) report(g, kErrInternal, 3);
+        return;
+    }
+    __syncwarp();
+    for (int j = lane_id(); j < (snc >> 2); j += 32) t4[j] = empty4();
+    __syncwarp();
+    __threadfence_block();
+    for (int j = lane_id(); j < written; j += 32) table_insert(g.slots, off, snc, ar[j]);
+    __syncwarp();
+    if (lane_id() == 0) {
+        g.cap[sx] = snc;
+        g.tomb[sx] = 0;
+    }
+}
+
 // After deletions: rebuild, in place and smaller, tables that became sparse or
 // full of tombstones (speed only; skipped when the scratch arena is full).
 // Small tables: one warp each; large ones (hubs): one block each.
 template <class Team>
-__device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
+__device__ void shrink_small(Team &T, const GraphCtx &g) {
     const int32_t tc = g.ctl->tcount;
     for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
         int i = i0 + lane_id();
@@ -541,44 +591,16 @@ __device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
         while (m) {
             int src = __ffs(m) - 1;
             m &= m - 1;
-            int32_t sx = __shfl_sync(kFull, x, src), snc = __shfl_sync(kFull, nc, src);
-            int32_t sc = __shfl_sync(kFull, c, src), sbase = __shfl_sync(kFull, base, src);
-            int32_t sd = __shfl_sync(kFull, d, src);
-            int64_t off = g.off[sx];
-            int4 *t4 = reinterpret_cast<int4 *>(g.slots + off);
-            int32_t *ar = g.arena + sbase;
-            int written = 0;
-            for (int j0 = 0; j0 < (sc >> 2); j0 += 32) {
-                int j = j0 + lane_id();
-                int4 q = j < (sc >> 2) ? t4[j] : empty4();
-                int cnt = (q.x >= 0) + (q.y >= 0) + (q.z >= 0) + (q.w >= 0);
-                int tot;
-                int ex = warp_exclusive(cnt, &tot);
-                int p = written + ex;
-                // the table holds exactly deg live keys; never write past the reservation
-                if (q.x >= 0 && p < sd) ar[p++] = q.x;
-                if (q.y >= 0 && p < sd) ar[p++] = q.y;
-                if (q.z >= 0 && p < sd) ar[p++] = q.z;
-                if (q.w >= 0 && p < sd) ar[p++] = q.w;
-                written += tot;
-            }
-            if (written != sd) {  // counters and table disagree: report, keep the table
-                if (lane_id() == 0) report(g, kErrInternal, 3);
-                continue;
-            }
-            __syncwarp();
-            for (int j = lane_id(); j < (snc >> 2); j += 32) t4[j] = empty4();
-            __syncwarp();
-            __threadfence_block();
-            for (int j = lane_id(); j < written; j += 32) table_insert(g.slots, off, snc, ar[j]);
-            __syncwarp();
-            if (lane_id() == 0) {
-                g.cap[sx] = snc;
-                g.tomb[sx] = 0;
-            }
+            shrink_table_warp(g, __shfl_sync(kFull, x, src), __shfl_sync(kFull, nc, src),
+                              __shfl_sync(kFull, c, src), __shfl_sync(kFull, base, src),
+                              __shfl_sync(kFull, d, src));
         }
     }
-    if (!T.sync()) return;
+}
+
+// The large tables listed by shrink_small: one block each.
+template <class Team>
+__device__ void shrink_big(Team &T, const GraphCtx &g, int *sh_scan) {
     const int32_t nbig = g.ctl->mcnt[1];
     for (int b = T.bid(); b < nbig; b += T.nthreads() / blockDim.x) {
         const int4 it = g.M[1][b];
@@ -613,8 +635,268 @@ __device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
             g.tomb[x] = 0;
         }
     }
+}
+
+template <class Team>
+__device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
+    shrink_small(T, g);
+    if (!T.sync()) return;
+    shrink_big(T, g, sh_scan);
     if (T.leader()) g.ctl->mcnt[1] = 0;
 }
+
+// ---------------------------------------------------------------------------
+// Split path: the steps before the rounds as free-standing kernels (single-graph
+// calls).  Appends to the shared lists and room taken from the pool or the shrink
+// arena are reserved once per block (block_reserve) instead of once per warp or
+// thread: with the whole GPU running these steps, per-warp atomics on one counter
+// serialise in L2.  Loops are block-strided so that every thread of a block runs
+// the same iterations.
+// ---------------------------------------------------------------------------
+
+// Every thread of the block calls with its amount (0: none); returns the position
+// of its first entry in the list whose length is *cnt (one global atomic per
+// block).  sh: blockDim.x / 32 + 1 slots of shared scratch.
+template <class C>
+__device__ C block_reserve(C *cnt, C amount, C *sh) {
+    const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    C incl = amount;
+    for (int o = 1; o < 32; o <<= 1) {
+        const C y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        C run = 0;
+        for (int k = 0; k < nw; ++k) {
+            const C t = sh[k];
+            sh[k] = run;
+            run += t;
+        }
+        sh[nw] = run ? atomicAdd(cnt, run) : (C)0;
+    }
+    __syncthreads();
+    const C pos = sh[nw] + sh[w] + incl - amount;
+    __syncthreads();  // sh is reused by the next call
+    return pos;
+}
+
+// Step A1 (split): as step_canonicalise.
+__device__ void pre_canon(const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
+    const int2 *e = reinterpret_cast<const int2 *>(in.edges);
+    unsigned long long loops = 0;
+    const int64_t mask = g.hcap - 1, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < in.B; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool fresh = false;
+        unsigned long long key = 0;
+        if (i < in.B) {
+            const int2 uv = e[i];
+            if (uv.x < 0 || uv.x >= g.n || uv.y < 0 || uv.y >= g.n) {
+                atomicOr(&g.ctl->err, kErrInvalidId);
+            } else if (uv.x == uv.y) {
+                loops++;
+            } else {
+                const int32_t a = min(uv.x, uv.y), b = max(uv.x, uv.y);
+                key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)b;
+                int64_t h = (int64_t)(mix64(key) & (uint64_t)mask);
+                for (int64_t it = 0; it <= mask; ++it) {
+                    const unsigned long long old = atomicCAS(&g.hset[h], kEmptyKey, key);
+                    if (old == kEmptyKey) { fresh = true; break; }
+                    if (old == key) break;
+                    h = (h + 1) & mask;
+                }
+            }
+        }
+        const unsigned long long pos = block_reserve<unsigned long long>(&g.ctl->ucount, fresh ? 1ull : 0ull, sh);
+        if (fresh) g.ukeys[pos] = key;
+    }
+    loops = warp_sum64(loops);
+    if (lane_id() == 0 && loops) atomicAdd(&g.ctl->st[kStSelfLoops], loops);
+}
+
+// Step A1, second half (split): as step_filter.
+__device__ void pre_filter(const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
+    const int64_t U = (int64_t)g.ctl->ucount, stride = (int64_t)gridDim.x * blockDim.x;
+    const int32_t stouch = in.stamp_base;
+    unsigned long long filtered = 0;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < U; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool keep = false;
+        unsigned long long key = 0;
+        int32_t u = 0, v = 0;
+        if (i < U) {
+            key = g.ukeys[i];
+            u = (int32_t)(key >> 32);
+            v = (int32_t)(key & 0xffffffffu);
+            const bool present = table_find(g.slots, g.off[u], g.cap[u], v);
+            keep = (in.op == kOpInsert) ? !present : present;
+            if (!keep) filtered++;
+        }
+        const bool tu = keep && atomicExch(&g.stamp[u], stouch) != stouch;
+        const bool tv = keep && atomicExch(&g.stamp[v], stouch) != stouch;
+        if (keep && in.op == kOpInsert) {
+            atomicAdd(&g.inc[u], 1);
+            atomicAdd(&g.inc[v], 1);
+        }
+        const unsigned long long pos = block_reserve<unsigned long long>(&g.ctl->vcount, keep ? 1ull : 0ull, sh);
+        if (keep) g.vkeys[pos] = key;
+        const unsigned long long pt =
+            block_reserve<unsigned long long>(&g.ctl->ttotal, (unsigned long long)(tu + tv), sh);
+        if (tu) g.touched[pt] = u;
+        if (tv) g.touched[pt + (tu ? 1 : 0)] = v;
+    }
+    filtered = warp_sum64(filtered);
+    if (lane_id() == 0 && filtered) atomicAdd(&g.ctl->st[kStFiltered], filtered);
+}
+
+// Step A2 (split): list the tables that must grow (M[0] = {x, new size}) and total
+// their sizes.  Run after pre_filter; tcount is taken from its touched total.
+__device__ void pre_grow_request(const GraphCtx &g, unsigned long long *sh) {
+    const int32_t tc = (int32_t)g.ctl->ttotal;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl->tcount = tc;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < tc; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool grow = false;
+        int32_t x = 0, nc = 0;
+        if (i < tc) {
+            x = g.touched[i];
+            const int64_t live = g.deg[x], tb = g.tomb[x], in = g.inc[x], c = g.cap[x];
+            if ((live + tb + in) * g.load_den > c * g.load_num) {
+                nc = next_pow2(2 * (live + in));
+                grow = true;
+            }
+        }
+        const unsigned long long pos = block_reserve<unsigned long long>(&g.ctl->gtotal, grow ? 1ull : 0ull, sh);
+        if (grow) g.M[0][pos] = make_int4(x, nc, 0, 0);
+        block_reserve<unsigned long long>(&g.ctl->grow_total, grow ? (unsigned long long)nc : 0ull, sh);
+    }
+}
+
+// The pool check before any table moves (split): every thread reads the same pool
+// top, since nothing is taken from the pool in this kernel.  When the pool cannot
+// take the growing tables, the batch's incoming counts are undone and the host
+// grows the pool and runs the batch again.
+__device__ void pre_pool_check(const GraphCtx &g) {
+    FreeTeam T;
+    if (*g.pool_top + g.ctl->grow_total <= (unsigned long long)g.pool_cap) return;
+    for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
+    if (T.leader()) atomicOr(&g.ctl->err, kErrNeedPool);
+}
+
+// Room in the pool for every growing table (split, after the check).
+__device__ void pre_alloc(const GraphCtx &g, unsigned long long *sh) {
+    const int64_t gc = (int64_t)g.ctl->gtotal, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < gc; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        const int4 it = i < gc ? g.M[0][i] : make_int4(0, 0, 0, 0);
+        const unsigned long long off =
+            block_reserve<unsigned long long>(g.pool_top, i < gc ? (unsigned long long)it.y : 0ull, sh);
+        if (i < gc) g.M[0][i] = make_int4(it.x, it.y, (int32_t)(off & 0xffffffffu), (int32_t)(off >> 32));
+    }
+}
+
+// Each growing table is moved by its owner -- a block for more than block_cap
+// slots, else a warp -- into its room: cleared, the old entries inserted, the
+// vertex pointed at it.  No other thread reads these vertices' tables meanwhile.
+__device__ void pre_grow(const GraphCtx &g) {
+    FreeTeam T;
+    const int32_t gc = (int32_t)g.ctl->gtotal;
+    for (int i = T.bid(); i < gc; i += gridDim.x) {  // large tables: whole block
+        const int4 it = g.M[0][i];
+        if (it.y <= g.block_cap) continue;  // block-uniform
+        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
+        for (int j = threadIdx.x; j < (it.y >> 2); j += blockDim.x) nt[j] = empty4();
+        __syncthreads();
+        const int32_t oc = g.cap[it.x];
+        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
+        for (int j = threadIdx.x; j < (oc >> 2); j += blockDim.x) {
+            const int4 q = ot[j];
+            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
+            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
+            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
+            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            g.off[it.x] = noff;
+            g.cap[it.x] = it.y;
+            g.tomb[it.x] = 0;
+        }
+    }
+    for (int i = T.wid(); i < gc; i += T.nwarps()) {  // small tables: one warp each
+        const int4 it = g.M[0][i];
+        if (it.y > g.block_cap) continue;
+        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
+        for (int j = lane_id(); j < (it.y >> 2); j += 32) nt[j] = empty4();
+        __syncwarp();
+        __threadfence_block();
+        const int32_t oc = g.cap[it.x];
+        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
+        for (int j = lane_id(); j < (oc >> 2); j += 32) {
+            const int4 q = ot[j];
+            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
+            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
+            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
+            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
+        }
+        __syncwarp();
+        if (lane_id() == 0) {
+            g.off[it.x] = noff;
+            g.cap[it.x] = it.y;
+            g.tomb[it.x] = 0;
+        }
+    }
+}
+
+// Shrink plan (split, after the deletions): tables that became sparse or full of
+// tombstones get arena room for their live keys and go to the warp list (M[0])
+// or, above block_cap slots, the block list (M[1]) as {x, new size, arena base,
+// live keys}; speed only, skipped when the arena is full.
+__device__ void pre_shrink_plan(const GraphCtx &g, unsigned long long *sh) {
+    const int32_t tc = (int32_t)g.ctl->ttotal;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl->tcount = tc;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < tc; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        int32_t x = 0, nc = 0, d = 0, c = 0;
+        bool want = false;
+        if (i < tc) {
+            x = g.touched[i];
+            d = g.deg[x];
+            c = g.cap[x];
+            const int32_t tb = g.tomb[x];
+            if (c > 4 && ((int64_t)d * 8 < c || (int64_t)tb * 4 > c)) {
+                nc = min(next_pow2(2 * (int64_t)d), c);  // in place: never larger than the region
+                want = nc < c || tb > 0;
+            }
+        }
+        const unsigned long long base =
+            block_reserve<unsigned long long>(&g.ctl->atotal, want ? (unsigned long long)d : 0ull, sh);
+        if (want && (int64_t)base + d > g.arena_cap) want = false;
+        const bool big = want && c > g.block_cap;
+        const unsigned long long ps = block_reserve<unsigned long long>(&g.ctl->gtotal, (want && !big) ? 1ull : 0ull, sh);
+        const unsigned long long pb = block_reserve<unsigned long long>(&g.ctl->btotal, big ? 1ull : 0ull, sh);
+        if (want && !big) g.M[0][ps] = make_int4(x, nc, (int32_t)base, d);
+        if (big) g.M[1][pb] = make_int4(x, nc, (int32_t)base, d);
+    }
+}
+
+// The warp list of the shrink plan: one warp per table.
+__device__ void pre_shrink_small(const GraphCtx &g) {
+    FreeTeam T;
+    const int32_t sc = (int32_t)g.ctl->gtotal;
+    for (int i = T.wid(); i < sc; i += T.nwarps()) {
+        const int4 it = g.M[0][i];
+        shrink_table_warp(g, it.x, it.y, g.cap[it.x], it.z, it.w);
+    }
+    if (T.leader()) g.ctl->mcnt[1] = (int32_t)g.ctl->btotal;  // the block list, for shrink_big
+}
+
 
 // ---------------------------------------------------------------------------
 // Mover scans.  Each moving vertex's table is scanned either by one thread
@@ -2522,7 +2804,9 @@ __device__ __forceinline__ void trace_steps(const GraphCtx &g, const uint64_t (&
     for (int i = 1; i < 12; ++i) rec[i] = (i < n) ? (int32_t)(t[i] - t[i - 1]) : 0;
 }
 
-template <class Team>
+// kRoundsOnly: the steps before the rounds already ran as separate kernels (the
+// single-graph calls); they are compiled out, leaving the rounds kernel leaner.
+template <class Team, bool kRoundsOnly = false>
 __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t *sh, int stage_shift) {
     int32_t *sh_upmax = sh;
     int32_t *sh_dnmin = sh + kMaxGroups;
@@ -2547,7 +2831,9 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
         g.ctl->trace_n = 1;
         tmark[nmark++] = global_ns();
     }
-    if (in.B > 0) {
+    if constexpr (kRoundsOnly) {  // a step kernel that failed stops the rounds too
+        if (ld_volatile(&g.ctl->err)) return;
+    } else if (in.B > 0) {
         step_canonicalise(T, g, in);
         if (!T.sync()) return;  // ids outside [0,n): nothing has changed
         if (tr) tmark[nmark++] = global_ns();
@@ -2556,23 +2842,25 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
         if (tr) tmark[nmark++] = global_ns();
     }
     if (in.op == kOpInsert) {
-        step_grow_request(T, g);
-        if (!T.sync()) return;
-        if (T.leader() && *g.pool_top + g.ctl->grow_total > (unsigned long long)g.pool_cap)
-            atomicOr(&g.ctl->err, kErrNeedPool);  // host grows the pool and runs the batch again
-        if (!T.sync()) {
-            // nothing but the batch's incoming counts has changed: undo them for the rerun
-            if (ld_volatile(&g.ctl->err) == kErrNeedPool)
-                for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
-            return;
+        if constexpr (!kRoundsOnly) {
+            step_grow_request(T, g);
+            if (!T.sync()) return;
+            if (T.leader() && *g.pool_top + g.ctl->grow_total > (unsigned long long)g.pool_cap)
+                atomicOr(&g.ctl->err, kErrNeedPool);  // host grows the pool and runs the batch again
+            if (!T.sync()) {
+                // nothing but the batch's incoming counts has changed: undo them for the rerun
+                if (ld_volatile(&g.ctl->err) == kErrNeedPool)
+                    for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
+                return;
+            }
+            if (tr) tmark[nmark++] = global_ns();
+            if (!step_grow_apply(T, g)) return;
+            if (!T.sync()) return;
+            if (tr) tmark[nmark++] = global_ns();
+            step_apply_insert(T, g);
+            if (!T.sync()) return;
+            if (tr) tmark[nmark++] = global_ns();
         }
-        if (tr) tmark[nmark++] = global_ns();
-        if (!step_grow_apply(T, g)) return;
-        if (!T.sync()) return;
-        if (tr) tmark[nmark++] = global_ns();
-        step_apply_insert(T, g);
-        if (!T.sync()) return;
-        if (tr) tmark[nmark++] = global_ns();
         if (!g.jump && !ins_sort_candidates(T, g, sh_scan)) return;
         if (tr) {
             tmark[nmark++] = global_ns();
@@ -2581,16 +2869,18 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
         if (g.jump) ins_rounds_jump(T, g, sh_upmax, whist, sh_block);
         else ins_rounds(T, g, sh_upmax, whist, stage_setup(sh_stage, stage_shift));
     } else {
-        if (T.leader()) {
-            g.ctl->nextmin[0] = kInf;
-            g.ctl->nextmin[1] = kInf;
+        if constexpr (!kRoundsOnly) {
+            if (T.leader()) {
+                g.ctl->nextmin[0] = kInf;
+                g.ctl->nextmin[1] = kInf;
+            }
+            step_apply_delete(T, g);
+            if (!T.sync()) return;
+            if (tr) tmark[nmark++] = global_ns();
+            step_shrink(T, g, sh_scan);
+            if (!T.sync()) return;
+            if (tr) tmark[nmark++] = global_ns();
         }
-        step_apply_delete(T, g);
-        if (!T.sync()) return;
-        if (tr) tmark[nmark++] = global_ns();
-        step_shrink(T, g, sh_scan);
-        if (!T.sync()) return;
-        if (tr) tmark[nmark++] = global_ns();
         unsigned long long evals = 0, evisits = 0;
         if (!dl_batch(T, g, g.touched, g.ctl->tcount, 0, -1, sh_dnmin, whist, sh_block, evals, evisits)) return;
         if (evals) {

@@ -87,6 +87,11 @@ struct Ctl {
     int32_t err_info[3];  // values seen by that check (diagnostics)
     int32_t trace_n;      // per-round records written
     int32_t rbcnt;        // violators with large tables (block-wide desire-level)
+    // split path (steps as separate kernels): list lengths reserved per block
+    unsigned long long ttotal;  // touched vertices
+    unsigned long long gtotal;  // growing tables (insert) / warp shrink list (delete)
+    unsigned long long btotal;  // block shrink list
+    unsigned long long atotal;  // shrink arena ints
     unsigned long long st[kStCount];
 };
 
@@ -102,6 +107,8 @@ struct GraphCtx {
     int32_t block_cap;     // tables above this many slots get a whole block (desire-levels, rebuilds)
     int32_t list_cap;      // insertion: chunk-scanned tables from this size on get an up-list
     int32_t jump;          // insertion violators move straight to their targets (jump variant)
+    int32_t pre_done;      // the steps before the rounds ran as separate kernels (plain form)
+    int32_t pad3;
     int64_t wait_limit_ns;
     const int32_t *upmax;  // [G]
     const int32_t *dnmin;  // [G]

@@ -37,7 +37,7 @@ class PldsStats(ctypes.Structure):
         "dl_evals", "dl_visits", "slots_scanned", "pool_slots_used", "pool_slots_cap", "device_bytes",
         "pool_grows", "err_bits", "err_site")] + [("err_info", ctypes.c_int64 * 3)] + \
         [(k, ctypes.c_int64) for k in ("kernel_ns", "launches", "up_visits", "affected", "skipped_rounds",
-                                        "skipped_moves", "skipped_visits", "skipped_up_visits")]
+                                        "skipped_moves", "skipped_visits", "skipped_up_visits", "pre_ns")]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "err_info"}
