@@ -81,9 +81,19 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_alloc(const __grid_constant
     pre_alloc(g, sh_res);
 }
 
+__global__ void __launch_bounds__(kPreThreads) k_pre_clear(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_clear(g);
+}
+
 __global__ void __launch_bounds__(kPreThreads) k_pre_grow(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     pre_grow(g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_commit(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_commit(g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_apply_insert(const __grid_constant__ GraphCtx g) {
@@ -538,9 +548,11 @@ static void launch_pre(plds *h, GraphCtx &g) {
         k_pre_grow_request<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_pool_check<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_alloc<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_clear<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_grow<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_commit<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_apply_insert<<<blocks, kPreThreads, 0, s>>>(g);
-        k += 5;
+        k += 7;
     } else {
         k_pre_apply_delete<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_shrink_plan<<<blocks, kPreThreads, 0, s>>>(g);

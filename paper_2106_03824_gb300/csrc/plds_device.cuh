@@ -781,12 +781,21 @@ __device__ void pre_grow_request(const GraphCtx &g, unsigned long long *sh) {
 // grows the pool and runs the batch again.
 __device__ void pre_pool_check(const GraphCtx &g) {
     FreeTeam T;
-    if (*g.pool_top + g.ctl->grow_total <= (unsigned long long)g.pool_cap) return;
+    const unsigned long long top = *g.pool_top;
+    if (top + g.ctl->grow_total <= (unsigned long long)g.pool_cap) {
+        if (T.leader()) g.ctl->pool_old = top;  // the new tables will fill [top, top + grow_total)
+        return;
+    }
     for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
     if (T.leader()) atomicOr(&g.ctl->err, kErrNeedPool);
 }
 
-// Room in the pool for every growing table (split, after the check).
+// Room in the pool for every growing table (split, after the check), and the
+// work list of the move: every old table cut into chunks of kGrowChunk slots,
+// items {growing-table index, chunk} in CL[0].  The rooms are contiguous from the
+// pool top read by the check.
+constexpr int kGrowChunk = 512;
+
 __device__ void pre_alloc(const GraphCtx &g, unsigned long long *sh) {
     const int64_t gc = (int64_t)g.ctl->gtotal, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < gc; b0 += stride) {
@@ -794,62 +803,58 @@ __device__ void pre_alloc(const GraphCtx &g, unsigned long long *sh) {
         const int4 it = i < gc ? g.M[0][i] : make_int4(0, 0, 0, 0);
         const unsigned long long off =
             block_reserve<unsigned long long>(g.pool_top, i < gc ? (unsigned long long)it.y : 0ull, sh);
-        if (i < gc) g.M[0][i] = make_int4(it.x, it.y, (int32_t)(off & 0xffffffffu), (int32_t)(off >> 32));
+        const int32_t nch = i < gc ? (g.cap[it.x] + kGrowChunk - 1) / kGrowChunk : 0;
+        const unsigned long long c0 = block_reserve<unsigned long long>(&g.ctl->ctotal, (unsigned long long)nch, sh);
+        if (i < gc) {
+            g.M[0][i] = make_int4(it.x, it.y, (int32_t)(off & 0xffffffffu), (int32_t)(off >> 32));
+            for (int32_t k = 0; k < nch; ++k) {
+                if ((int64_t)(c0 + k) < g.clcap) g.CL[0][c0 + k] = make_int4((int32_t)i, k, 0, 0);
+                else report(g, kErrListOverflow, 23, (int32_t)i, k, 0);
+            }
+        }
     }
 }
 
-// Each growing table is moved by its owner -- a block for more than block_cap
-// slots, else a warp -- into its room: cleared, the old entries inserted, the
-// vertex pointed at it.  No other thread reads these vertices' tables meanwhile.
+// Every new table starts empty: one fill of the contiguous rooms.
+__device__ void pre_clear(const GraphCtx &g) {
+    FreeTeam T;
+    int4 *p = reinterpret_cast<int4 *>(g.slots + g.ctl->pool_old);
+    const int64_t n4 = (int64_t)(g.ctl->grow_total >> 2);
+    for (int64_t j = T.tid(); j < n4; j += T.nthreads()) p[j] = empty4();
+}
+
+// The old entries go into the new tables, one warp per chunk of an old table (a
+// hub's table is spread over many warps).  The vertices still point at their old
+// tables; pre_commit repoints them afterwards.
 __device__ void pre_grow(const GraphCtx &g) {
     FreeTeam T;
-    const int32_t gc = (int32_t)g.ctl->gtotal;
-    for (int i = T.bid(); i < gc; i += gridDim.x) {  // large tables: whole block
-        const int4 it = g.M[0][i];
-        if (it.y <= g.block_cap) continue;  // block-uniform
+    const int64_t nc_items = (int64_t)g.ctl->ctotal;
+    for (int64_t c = T.wid(); c < nc_items; c += T.nwarps()) {
+        const int4 ci = g.CL[0][c];
+        const int4 it = g.M[0][ci.x];
         const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
-        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
-        for (int j = threadIdx.x; j < (it.y >> 2); j += blockDim.x) nt[j] = empty4();
-        __syncthreads();
         const int32_t oc = g.cap[it.x];
         const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
-        for (int j = threadIdx.x; j < (oc >> 2); j += blockDim.x) {
+        const int j_end = min(oc, (ci.y + 1) * kGrowChunk) >> 2;
+        for (int j = (ci.y * kGrowChunk >> 2) + lane_id(); j < j_end; j += 32) {
             const int4 q = ot[j];
             if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
             if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
             if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
             if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            g.off[it.x] = noff;
-            g.cap[it.x] = it.y;
-            g.tomb[it.x] = 0;
         }
     }
-    for (int i = T.wid(); i < gc; i += T.nwarps()) {  // small tables: one warp each
+}
+
+// Every growing vertex points at its new table.
+__device__ void pre_commit(const GraphCtx &g) {
+    FreeTeam T;
+    const int64_t gc = (int64_t)g.ctl->gtotal;
+    for (int64_t i = T.tid(); i < gc; i += T.nthreads()) {
         const int4 it = g.M[0][i];
-        if (it.y > g.block_cap) continue;
-        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
-        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
-        for (int j = lane_id(); j < (it.y >> 2); j += 32) nt[j] = empty4();
-        __syncwarp();
-        __threadfence_block();
-        const int32_t oc = g.cap[it.x];
-        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
-        for (int j = lane_id(); j < (oc >> 2); j += 32) {
-            const int4 q = ot[j];
-            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
-            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
-            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
-            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
-        }
-        __syncwarp();
-        if (lane_id() == 0) {
-            g.off[it.x] = noff;
-            g.cap[it.x] = it.y;
-            g.tomb[it.x] = 0;
-        }
+        g.off[it.x] = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
+        g.cap[it.x] = it.y;
+        g.tomb[it.x] = 0;
     }
 }
 
