@@ -118,16 +118,19 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_shrink_plan(const __grid_co
     pre_shrink_plan(g, sh_res);
 }
 
-__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_small(const __grid_constant__ GraphCtx g) {
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_a(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_shrink_small(g);
+    pre_shrink_a(g);
 }
 
-__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_big(const __grid_constant__ GraphCtx g) {
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_b(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    __shared__ int sh_scan[64];
-    FreeTeam T;
-    shrink_big(T, g, sh_scan);
+    pre_shrink_b(g);
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_pre_shrink_c(const __grid_constant__ GraphCtx g) {
+    if (ld_volatile(&g.ctl->err)) return;
+    pre_shrink_c(g);
 }
 
 // Coreness estimate (Definition "Coreness Estimate"): exponent
@@ -396,7 +399,9 @@ static int grow_pool(plds *h, int64_t extra) {
     cudaStreamSynchronize(h->stream);
     int rc = cuda_check(h);
     if (rc) return rc;
-    int64_t want = std::max<int64_t>(h->pool_cap, 2 * (live + extra));
+    // four times the live slots: every growth costs a stopped attempt, a copy of the
+    // pool and a rerun, so fewer of them pay for the extra room (capped by free HBM)
+    int64_t want = std::max<int64_t>(h->pool_cap, 4 * (live + extra));
     want = (want + 3) & ~(int64_t)3;
     // gate on free HBM (keep kHbmReserve free for everything else on the device)
     // and on the pool limit, if one is set
@@ -556,9 +561,10 @@ static void launch_pre(plds *h, GraphCtx &g) {
     } else {
         k_pre_apply_delete<<<blocks, kPreThreads, 0, s>>>(g);
         k_pre_shrink_plan<<<blocks, kPreThreads, 0, s>>>(g);
-        k_pre_shrink_small<<<blocks, kPreThreads, 0, s>>>(g);
-        k_pre_shrink_big<<<blocks, kPreThreads, 0, s>>>(g);
-        k += 4;
+        k_pre_shrink_a<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_shrink_b<<<blocks, kPreThreads, 0, s>>>(g);
+        k_pre_shrink_c<<<blocks, kPreThreads, 0, s>>>(g);
+        k += 5;
     }
     cudaEventRecord(h->evm, s);
     h->launches += k;

@@ -858,10 +858,16 @@ __device__ void pre_commit(const GraphCtx &g) {
     }
 }
 
+__device__ __forceinline__ void shrink_item(const GraphCtx &g, int list, unsigned long long pos, int32_t j, int32_t k) {
+    if ((int64_t)pos < g.clcap) g.CL[list][pos] = make_int4(j, k, 0, 0);
+    else report(g, kErrListOverflow, 24, j, k, list);
+}
+
 // Shrink plan (split, after the deletions): tables that became sparse or full of
 // tombstones get arena room for their live keys and go to the warp list (M[0])
-// or, above block_cap slots, the block list (M[1]) as {x, new size, arena base,
-// live keys}; speed only, skipped when the arena is full.
+// or, above block_cap slots, the large list (M[1]) as {x, new size, arena base,
+// live keys}, whose rebuild is cut into chunks; speed only, skipped when the
+// arena is full.
 __device__ void pre_shrink_plan(const GraphCtx &g, unsigned long long *sh) {
     const int32_t tc = (int32_t)g.ctl->ttotal;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -887,19 +893,100 @@ __device__ void pre_shrink_plan(const GraphCtx &g, unsigned long long *sh) {
         const unsigned long long ps = block_reserve<unsigned long long>(&g.ctl->gtotal, (want && !big) ? 1ull : 0ull, sh);
         const unsigned long long pb = block_reserve<unsigned long long>(&g.ctl->btotal, big ? 1ull : 0ull, sh);
         if (want && !big) g.M[0][ps] = make_int4(x, nc, (int32_t)base, d);
-        if (big) g.M[1][pb] = make_int4(x, nc, (int32_t)base, d);
+        if (big) {
+            g.M[1][pb] = make_int4(x, nc, (int32_t)base, d);
+            g.lfill[0][x] = 0;  // cursor of the compaction into the arena room
+        }
+        // a large table's work in chunks of kGrowChunk: compaction of its c slots,
+        // clearing of its nc new slots, insertion of its d keys (lists CL[0..2])
+        const int32_t n0 = big ? (c + kGrowChunk - 1) / kGrowChunk : 0;
+        const int32_t n1 = big ? (nc + kGrowChunk - 1) / kGrowChunk : 0;
+        const int32_t n2 = big ? (d + kGrowChunk - 1) / kGrowChunk : 0;
+        const unsigned long long c0 = block_reserve<unsigned long long>(&g.ctl->ctotal, (unsigned long long)n0, sh);
+        const unsigned long long c1 = block_reserve<unsigned long long>(&g.ctl->c1total, (unsigned long long)n1, sh);
+        const unsigned long long c2 = block_reserve<unsigned long long>(&g.ctl->c2total, (unsigned long long)n2, sh);
+        for (int32_t k = 0; k < n0; ++k) shrink_item(g, 0, c0 + k, (int32_t)pb, k);
+        for (int32_t k = 0; k < n1; ++k) shrink_item(g, 1, c1 + k, (int32_t)pb, k);
+        for (int32_t k = 0; k < n2; ++k) shrink_item(g, 2, c2 + k, (int32_t)pb, k);
     }
 }
 
-// The warp list of the shrink plan: one warp per table.
-__device__ void pre_shrink_small(const GraphCtx &g) {
+// Shrink, first pass: the small tables rebuilt whole, one warp each; the large
+// tables' live keys copied into their arena room, one warp per chunk of slots.
+__device__ void pre_shrink_a(const GraphCtx &g) {
     FreeTeam T;
     const int32_t sc = (int32_t)g.ctl->gtotal;
     for (int i = T.wid(); i < sc; i += T.nwarps()) {
         const int4 it = g.M[0][i];
         shrink_table_warp(g, it.x, it.y, g.cap[it.x], it.z, it.w);
     }
-    if (T.leader()) g.ctl->mcnt[1] = (int32_t)g.ctl->btotal;  // the block list, for shrink_big
+    const int64_t n0 = (int64_t)g.ctl->ctotal;
+    for (int64_t c = T.wid(); c < n0; c += T.nwarps()) {
+        const int4 ci = g.CL[0][c];
+        const int4 it = g.M[1][ci.x];
+        const int32_t oc = g.cap[it.x];
+        const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
+        const int j = (ci.y * kGrowChunk >> 2) + lane_id();  // kGrowChunk = 4 x 32 x 4 slots
+        int32_t ks[16];
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int4 q = (j + 32 * u) < (oc >> 2) && (j + 32 * u) < ((ci.y + 1) * kGrowChunk >> 2) ? t4[j + 32 * u]
+                                                                                                     : empty4();
+            ks[4 * u] = q.x; ks[4 * u + 1] = q.y; ks[4 * u + 2] = q.z; ks[4 * u + 3] = q.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) cnt += ks[q] >= 0;
+        int tot;
+        const int ex = warp_exclusive(cnt, &tot);
+        int base = 0;
+        if (lane_id() == 0 && tot) base = atomicAdd(&g.lfill[0][it.x], tot);
+        int p = __shfl_sync(kFull, base, 0) + ex;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (ks[q] >= 0) {
+                if (p < it.w) g.arena[it.z + p] = ks[q];  // never past the room (checked below)
+                ++p;
+            }
+    }
+}
+
+// Shrink, second pass: a large table whose copy holds exactly its live keys is
+// cleared (its first nc slots) and takes its new size; otherwise it is reported
+// and kept.
+__device__ void pre_shrink_b(const GraphCtx &g) {
+    FreeTeam T;
+    const int64_t n1 = (int64_t)g.ctl->c1total;
+    for (int64_t c = T.wid(); c < n1; c += T.nwarps()) {
+        const int4 ci = g.CL[1][c];
+        const int4 it = g.M[1][ci.x];
+        if (g.lfill[0][it.x] != it.w) {
+            if (ci.y == 0 && lane_id() == 0) report(g, kErrInternal, 3, it.x, g.lfill[0][it.x], it.w);
+            continue;
+        }
+        int4 *t4 = reinterpret_cast<int4 *>(g.slots + g.off[it.x]);
+        const int j_end = min(it.y, (ci.y + 1) * kGrowChunk) >> 2;
+        for (int j = (ci.y * kGrowChunk >> 2) + lane_id(); j < j_end; j += 32) t4[j] = empty4();
+        if (ci.y == 0 && lane_id() == 0) {
+            g.cap[it.x] = it.y;
+            g.tomb[it.x] = 0;
+        }
+    }
+}
+
+// Shrink, third pass: the copied keys go back into the cleared tables, one warp
+// per chunk of keys.
+__device__ void pre_shrink_c(const GraphCtx &g) {
+    FreeTeam T;
+    const int64_t n2 = (int64_t)g.ctl->c2total;
+    for (int64_t c = T.wid(); c < n2; c += T.nwarps()) {
+        const int4 ci = g.CL[2][c];
+        const int4 it = g.M[1][ci.x];
+        if (g.lfill[0][it.x] != it.w) continue;  // reported and kept in the second pass
+        const int64_t off = g.off[it.x];
+        const int k_end = min(it.w, (ci.y + 1) * kGrowChunk);
+        for (int k = ci.y * kGrowChunk + lane_id(); k < k_end; k += 32) table_insert(g.slots, off, it.y, g.arena[it.z + k]);
+    }
 }
 
 

@@ -92,7 +92,9 @@ struct Ctl {
     unsigned long long gtotal;  // growing tables (insert) / warp shrink list (delete)
     unsigned long long btotal;  // block shrink list
     unsigned long long atotal;  // shrink arena ints
-    unsigned long long ctotal;  // chunks of the old tables of growing vertices
+    unsigned long long ctotal;  // chunks of the old tables of growing vertices / of large tables to shrink
+    unsigned long long c1total;  // chunks of the large shrinking tables' new slots (clear)
+    unsigned long long c2total;  // chunks of their live keys (reinsert)
     unsigned long long pool_old;  // pool top before the growing tables took their room
     unsigned long long st[kStCount];
 };
