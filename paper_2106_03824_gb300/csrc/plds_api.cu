@@ -1,9 +1,11 @@
 // Host runtime and C ABI of the GB300 PLDS (declared in include/plds.h).
 //
-// One batch call = one cooperative kernel launch that runs every step of the
-// batch (preprocessing, table growth, adjacency update, counters, level rounds)
-// with grid-wide barriers between steps, followed by one read of the control
-// words.  Device memory comes from the caller's allocator (default:
+// One batch call = the steps before the level rounds (preprocessing, table
+// growth or shrinking, adjacency and counter updates) as plain full-occupancy
+// kernels, then one cooperative kernel for the level rounds with grid-wide
+// barriers between rounds, followed by one read of the control words.  The
+// serving and batched forms run the same device steps inside their persistent
+// kernels with team barriers between them.  Device memory comes from the caller's allocator (default:
 // cudaMallocAsync on the handle's stream).
 #include <cuda_runtime.h>
 
@@ -50,50 +52,56 @@ __global__ void __launch_bounds__(512) k_batch_grid(const __grid_constant__ Grap
 // starts by reading the error word: a step that failed (bad id, pool too small)
 // stops the rest, and the cooperative rounds kernel after them as well.
 constexpr int kPreThreads = 256;
-#define PRE_SCRATCH __shared__ unsigned long long sh_res[kPreThreads / 32 + 1]
+#define PRE_SCRATCH             \
+    FreeTeam T;                 \
+    __shared__ unsigned long long sh_res[kPreThreads / 32 + 1]
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_canon(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     PRE_SCRATCH;
-    pre_canon(g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+    pre_canon(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_filter(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     PRE_SCRATCH;
-    pre_filter(g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+    pre_filter(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_grow_request(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     PRE_SCRATCH;
-    pre_grow_request(g, sh_res);
+    pre_grow_request(T, g, sh_res);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_pool_check(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_pool_check(g);
+    FreeTeam T;
+    pre_pool_check(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_alloc(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     PRE_SCRATCH;
-    pre_alloc(g, sh_res);
+    pre_alloc(T, g, sh_res);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_clear(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_clear(g);
+    FreeTeam T;
+    pre_clear(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_grow(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_grow(g);
+    FreeTeam T;
+    pre_grow(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_commit(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_commit(g);
+    FreeTeam T;
+    pre_commit(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_apply_insert(const __grid_constant__ GraphCtx g) {
@@ -115,22 +123,25 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_apply_delete(const __grid_c
 __global__ void __launch_bounds__(kPreThreads) k_pre_shrink_plan(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
     PRE_SCRATCH;
-    pre_shrink_plan(g, sh_res);
+    pre_shrink_plan(T, g, sh_res);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_shrink_a(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_shrink_a(g);
+    FreeTeam T;
+    pre_shrink_a(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_shrink_b(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_shrink_b(g);
+    FreeTeam T;
+    pre_shrink_b(T, g);
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_shrink_c(const __grid_constant__ GraphCtx g) {
     if (ld_volatile(&g.ctl->err)) return;
-    pre_shrink_c(g);
+    FreeTeam T;
+    pre_shrink_c(T, g);
 }
 
 // Coreness estimate (Definition "Coreness Estimate"): exponent

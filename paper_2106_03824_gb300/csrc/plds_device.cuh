@@ -42,6 +42,7 @@ struct GridTeam {
     __device__ int wid() const { return tid() >> 5; }
     __device__ int nwarps() const { return nthreads() >> 5; }
     __device__ int bid() const { return blockIdx.x; }
+    __device__ int nblocks() const { return gridDim.x; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
     // Grid-wide barrier with a bounded wait: a block that waits longer than
     // limit_ns (or sees the error word set) records kErrTimeout and leaves.
@@ -107,6 +108,7 @@ struct BlockTeam {
     __device__ int wid() const { return threadIdx.x >> 5; }
     __device__ int nwarps() const { return blockDim.x >> 5; }
     __device__ int bid() const { return 0; }
+    __device__ int nblocks() const { return 1; }
     __device__ bool leader() const { return threadIdx.x == 0; }
     __device__ bool sync() {
         __threadfence_block();
@@ -126,6 +128,7 @@ struct FreeTeam {
     __device__ int wid() const { return tid() >> 5; }
     __device__ int nwarps() const { return nthreads() >> 5; }
     __device__ int bid() const { return blockIdx.x; }
+    __device__ int nblocks() const { return gridDim.x; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
 };
 
@@ -151,16 +154,6 @@ __device__ __forceinline__ int warp_append(int32_t *counter, bool pred) {
     if (lane_id() == leader) base = atomicAdd(counter, __popc(m));
     base = __shfl_sync(kFull, base, leader);
     return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
-}
-
-__device__ __forceinline__ long long warp_append64(unsigned long long *counter, bool pred) {
-    unsigned m = __ballot_sync(kFull, pred);
-    if (m == 0) return -1;
-    int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane_id() == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    return pred ? (long long)(base + __popc(m & ((1u << lane_id()) - 1u))) : -1;
 }
 
 // Exclusive warp prefix sum; *total gets the warp total.
@@ -308,171 +301,6 @@ __device__ int block_exclusive(int x, int *sh32, int *total) {
     return r;
 }
 
-// ---------------------------------------------------------------------------
-// Step A1: canonicalise + validate.  Drops self-loops, keys each edge as
-// (min,max), keeps one copy of each key (batch hash set), flags ids outside [0,n).
-// ---------------------------------------------------------------------------
-template <class Team>
-__device__ void step_canonicalise(Team &T, const GraphCtx &g, const BatchIn &in) {
-    const int2 *e = reinterpret_cast<const int2 *>(in.edges);
-    unsigned long long loops = 0;
-    const int64_t mask = g.hcap - 1;
-    for (int64_t i0 = (int64_t)T.wid() * 32; i0 < in.B; i0 += (int64_t)T.nwarps() * 32) {
-        int64_t i = i0 + lane_id();
-        bool fresh = false;
-        unsigned long long key = 0;
-        if (i < in.B) {
-            int2 uv = e[i];
-            if (uv.x < 0 || uv.x >= g.n || uv.y < 0 || uv.y >= g.n) {
-                atomicOr(&g.ctl->err, kErrInvalidId);
-            } else if (uv.x == uv.y) {
-                loops++;
-            } else {
-                int32_t a = min(uv.x, uv.y), b = max(uv.x, uv.y);
-                key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)b;
-                int64_t h = (int64_t)(mix64(key) & (uint64_t)mask);
-                for (int64_t it = 0; it <= mask; ++it) {
-                    unsigned long long old = atomicCAS(&g.hset[h], kEmptyKey, key);
-                    if (old == kEmptyKey) { fresh = true; break; }
-                    if (old == key) break;
-                    h = (h + 1) & mask;
-                }
-            }
-        }
-        long long pos = warp_append64(&g.ctl->ucount, fresh);
-        if (fresh) g.ukeys[pos] = key;
-    }
-    if (loops) atomicAdd(&g.ctl->st[kStSelfLoops], loops);
-}
-
-// Step A1 (second half): keep insertions of absent / deletions of present edges;
-// collect the touched endpoints (deduplicated by stamp) and, for insertions, the
-// number of incoming edges per endpoint.
-template <class Team>
-__device__ void step_filter(Team &T, const GraphCtx &g, const BatchIn &in) {
-    const int64_t U = (int64_t)g.ctl->ucount;
-    const int32_t stouch = in.stamp_base;
-    unsigned long long filtered = 0;
-    for (int64_t i0 = (int64_t)T.wid() * 32; i0 < U; i0 += (int64_t)T.nwarps() * 32) {
-        int64_t i = i0 + lane_id();
-        bool keep = false;
-        unsigned long long key = 0;
-        int32_t u = 0, v = 0;
-        if (i < U) {
-            key = g.ukeys[i];
-            u = (int32_t)(key >> 32);
-            v = (int32_t)(key & 0xffffffffu);
-            bool present = table_find(g.slots, g.off[u], g.cap[u], v);
-            keep = (in.op == kOpInsert) ? !present : present;
-            if (!keep) filtered++;
-        }
-        long long pos = warp_append64(&g.ctl->vcount, keep);
-        if (keep) g.vkeys[pos] = key;
-        bool tu = keep && atomicExch(&g.stamp[u], stouch) != stouch;
-        int pu = warp_append(&g.ctl->tcount, tu);
-        if (tu) g.touched[pu] = u;
-        bool tv = keep && atomicExch(&g.stamp[v], stouch) != stouch;
-        int pv = warp_append(&g.ctl->tcount, tv);
-        if (tv) g.touched[pv] = v;
-        if (keep && in.op == kOpInsert) {
-            atomicAdd(&g.inc[u], 1);
-            atomicAdd(&g.inc[v], 1);
-        }
-    }
-    if (filtered) atomicAdd(&g.ctl->st[kStFiltered], filtered);
-}
-
-// Step A2 (insert): tables whose load would pass load_num/load_den get a new,
-// larger table.  First pass: list them and total the requested slots.
-template <class Team>
-__device__ void step_grow_request(Team &T, const GraphCtx &g) {
-    const int32_t tc = g.ctl->tcount;
-    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
-        int i = i0 + lane_id();
-        bool grow = false;
-        int32_t x = 0, nc = 0;
-        if (i < tc) {
-            x = g.touched[i];
-            int64_t live = g.deg[x], tb = g.tomb[x], in = g.inc[x], c = g.cap[x];
-            if ((live + tb + in) * g.load_den > c * g.load_num) {
-                nc = next_pow2(2 * (live + in));
-                grow = true;
-            }
-        }
-        int pos = warp_append(&g.ctl->mcnt[0], grow);
-        if (grow) {
-            g.M[0][pos] = make_int4(x, nc, 0, 0);
-            atomicAdd(&g.ctl->grow_total, (unsigned long long)nc);
-        }
-    }
-}
-
-// Second pass (after the pool check): allocate and rehash.  Small tables: one
-// warp each.  Large tables (hubs): one block each, so a hub's rebuild is not
-// left to a single warp.
-template <class Team>
-__device__ bool step_grow_apply(Team &T, const GraphCtx &g) {
-    const int32_t gc = g.ctl->mcnt[0];
-    for (int i = T.tid(); i < gc; i += T.nthreads()) {
-        const int4 it = g.M[0][i];
-        const unsigned long long noff = atomicAdd(g.pool_top, (unsigned long long)it.y);
-        const int4 rec = make_int4(it.x, it.y, (int32_t)(noff & 0xffffffffu), (int32_t)(noff >> 32));
-        g.M[0][i] = rec;
-        if (it.y > g.block_cap) {
-            const int b = atomicAdd(&g.ctl->mcnt[1], 1);
-            g.M[1][b] = rec;
-        }
-    }
-    if (!T.sync()) return false;
-    for (int i = T.wid(); i < gc; i += T.nwarps()) {
-        const int4 it = g.M[0][i];
-        const int32_t x = it.x, nc = it.y;
-        if (nc > g.block_cap) continue;
-        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
-        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
-        for (int j = lane_id(); j < (nc >> 2); j += 32) nt[j] = empty4();
-        __syncwarp();
-        __threadfence_block();
-        const int32_t oc = g.cap[x];
-        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[x]);
-        for (int j = lane_id(); j < (oc >> 2); j += 32) {
-            const int4 q = ot[j];
-            if (q.x >= 0) table_insert(g.slots, noff, nc, q.x);
-            if (q.y >= 0) table_insert(g.slots, noff, nc, q.y);
-            if (q.z >= 0) table_insert(g.slots, noff, nc, q.z);
-            if (q.w >= 0) table_insert(g.slots, noff, nc, q.w);
-        }
-    }
-    // large tables: one block each (blocks work on different tables in parallel)
-    const int32_t nbig = g.ctl->mcnt[1];
-    for (int b = T.bid(); b < nbig; b += T.nthreads() / blockDim.x) {
-        const int4 it = g.M[1][b];
-        const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
-        int4 *nt = reinterpret_cast<int4 *>(g.slots + noff);
-        for (int j = threadIdx.x; j < (it.y >> 2); j += blockDim.x) nt[j] = empty4();
-        __syncthreads();
-        const int32_t oc = g.cap[it.x];
-        const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
-        for (int j = threadIdx.x; j < (oc >> 2); j += blockDim.x) {
-            const int4 q = ot[j];
-            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
-            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
-            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
-            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
-        }
-        __syncthreads();
-    }
-    if (!T.sync()) return false;
-    for (int i = T.tid(); i < gc; i += T.nthreads()) {
-        const int4 it = g.M[0][i];
-        g.off[it.x] = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
-        g.cap[it.x] = it.y;
-        g.tomb[it.x] = 0;
-    }
-    if (T.leader()) g.ctl->mcnt[1] = 0;
-    return true;
-}
-
 // Steps A2+A3 (insert): put both directions into the tables and update deg, up
 // (other endpoint on a level >= own) and up* (other endpoint on a level >= own-1).
 template <class Team>
@@ -556,102 +384,13 @@ __device__ __forceinline__ void shrink_table_warp(const GraphCtx &g, int32_t sx,
     }
 }
 
-// After deletions: rebuild, in place and smaller, tables that became sparse or
-// full of tombstones (speed only; skipped when the scratch arena is full).
-// Small tables: one warp each; large ones (hubs): one block each.
-template <class Team>
-__device__ void shrink_small(Team &T, const GraphCtx &g) {
-    const int32_t tc = g.ctl->tcount;
-    for (int i0 = T.wid() * 32; i0 < tc; i0 += T.nwarps() * 32) {
-        int i = i0 + lane_id();
-        int32_t x = 0, nc = 0, d = 0, c = 0;
-        bool want = false;
-        if (i < tc) {
-            x = g.touched[i];
-            d = g.deg[x];
-            c = g.cap[x];
-            int32_t tb = g.tomb[x];
-            if (c > 4 && ((int64_t)d * 8 < c || (int64_t)tb * 4 > c)) {
-                // rebuilt in place, so never larger than the current region (d < c always)
-                nc = min(next_pow2(2 * (int64_t)d), c);
-                want = nc < c || tb > 0;
-            }
-        }
-        int base = -1;
-        if (want) {
-            base = atomicAdd(&g.ctl->shrink_used, d);
-            if ((int64_t)base + d > g.arena_cap) want = false;
-        }
-        const bool big = want && c > g.block_cap;
-        if (big) {  // a whole block rebuilds it below
-            const int b = atomicAdd(&g.ctl->mcnt[1], 1);
-            g.M[1][b] = make_int4(x, nc, base, d);
-        }
-        unsigned m = __ballot_sync(kFull, want && !big);
-        while (m) {
-            int src = __ffs(m) - 1;
-            m &= m - 1;
-            shrink_table_warp(g, __shfl_sync(kFull, x, src), __shfl_sync(kFull, nc, src),
-                              __shfl_sync(kFull, c, src), __shfl_sync(kFull, base, src),
-                              __shfl_sync(kFull, d, src));
-        }
-    }
-}
-
-// The large tables listed by shrink_small: one block each.
-template <class Team>
-__device__ void shrink_big(Team &T, const GraphCtx &g, int *sh_scan) {
-    const int32_t nbig = g.ctl->mcnt[1];
-    for (int b = T.bid(); b < nbig; b += T.nthreads() / blockDim.x) {
-        const int4 it = g.M[1][b];
-        const int32_t x = it.x, nc = it.y, abase = it.z, d = it.w, c = g.cap[x];
-        const int64_t off = g.off[x];
-        int4 *t4 = reinterpret_cast<int4 *>(g.slots + off);
-        int32_t *ar = g.arena + abase;
-        int written = 0;
-        for (int j0 = 0; j0 < (c >> 2); j0 += blockDim.x) {
-            const int j = j0 + threadIdx.x;
-            const int4 q = j < (c >> 2) ? t4[j] : empty4();
-            const int cnt = (q.x >= 0) + (q.y >= 0) + (q.z >= 0) + (q.w >= 0);
-            int tot;
-            int p = written + block_exclusive(cnt, sh_scan, &tot);
-            if (q.x >= 0 && p < d) ar[p++] = q.x;
-            if (q.y >= 0 && p < d) ar[p++] = q.y;
-            if (q.z >= 0 && p < d) ar[p++] = q.z;
-            if (q.w >= 0 && p < d) ar[p++] = q.w;
-            written += tot;
-        }
-        if (written != d) {
-            if (threadIdx.x == 0) report(g, kErrInternal, 3);
-            continue;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < (nc >> 2); j += blockDim.x) t4[j] = empty4();
-        __syncthreads();
-        for (int j = threadIdx.x; j < written; j += blockDim.x) table_insert(g.slots, off, nc, ar[j]);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            g.cap[x] = nc;
-            g.tomb[x] = 0;
-        }
-    }
-}
-
-template <class Team>
-__device__ void step_shrink(Team &T, const GraphCtx &g, int *sh_scan) {
-    shrink_small(T, g);
-    if (!T.sync()) return;
-    shrink_big(T, g, sh_scan);
-    if (T.leader()) g.ctl->mcnt[1] = 0;
-}
-
 // ---------------------------------------------------------------------------
-// Split path: the steps before the rounds as free-standing kernels (single-graph
-// calls).  Appends to the shared lists and room taken from the pool or the shrink
-// arena are reserved once per block (block_reserve) instead of once per warp or
-// thread: with the whole GPU running these steps, per-warp atomics on one counter
-// serialise in L2.  Loops are block-strided so that every thread of a block runs
-// the same iterations.
+// Steps A1-A2 for any team: between two steps a team barrier, or, for the
+// single-graph calls, a kernel boundary (each step its own full-occupancy kernel
+// with a FreeTeam).  Appends to the shared lists and room taken from the pool or
+// the shrink arena are reserved once per block (block_reserve) instead of once per
+// warp or thread: per-warp atomics on one counter serialise in L2.  Loops over
+// lists are block-strided so that every thread of a block runs the same iterations.
 // ---------------------------------------------------------------------------
 
 // Every thread of the block calls with its amount (0: none); returns the position
@@ -682,12 +421,14 @@ __device__ C block_reserve(C *cnt, C amount, C *sh) {
     return pos;
 }
 
-// Step A1 (split): as step_canonicalise.
-__device__ void pre_canon(const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
+// Step A1: canonicalise + validate.  Drops self-loops, keys each edge as
+// (min,max), keeps one copy of each key (batch hash set), flags ids outside [0,n).
+template <class Team>
+__device__ void pre_canon(Team &T, const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
     const int2 *e = reinterpret_cast<const int2 *>(in.edges);
     unsigned long long loops = 0;
-    const int64_t mask = g.hcap - 1, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < in.B; b0 += stride) {
+    const int64_t mask = g.hcap - 1, stride = (int64_t)T.nblocks() * blockDim.x;
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < in.B; b0 += stride) {
         const int64_t i = b0 + threadIdx.x;
         bool fresh = false;
         unsigned long long key = 0;
@@ -716,12 +457,15 @@ __device__ void pre_canon(const GraphCtx &g, const BatchIn &in, unsigned long lo
     if (lane_id() == 0 && loops) atomicAdd(&g.ctl->st[kStSelfLoops], loops);
 }
 
-// Step A1, second half (split): as step_filter.
-__device__ void pre_filter(const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
-    const int64_t U = (int64_t)g.ctl->ucount, stride = (int64_t)gridDim.x * blockDim.x;
+// Step A1, second half: keep insertions of absent / deletions of present edges;
+// collect the touched endpoints (deduplicated by stamp) and, for insertions, the
+// number of incoming edges per endpoint.
+template <class Team>
+__device__ void pre_filter(Team &T, const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
+    const int64_t U = (int64_t)g.ctl->ucount, stride = (int64_t)T.nblocks() * blockDim.x;
     const int32_t stouch = in.stamp_base;
     unsigned long long filtered = 0;
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < U; b0 += stride) {
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < U; b0 += stride) {
         const int64_t i = b0 + threadIdx.x;
         bool keep = false;
         unsigned long long key = 0;
@@ -751,13 +495,15 @@ __device__ void pre_filter(const GraphCtx &g, const BatchIn &in, unsigned long l
     if (lane_id() == 0 && filtered) atomicAdd(&g.ctl->st[kStFiltered], filtered);
 }
 
-// Step A2 (split): list the tables that must grow (M[0] = {x, new size}) and total
-// their sizes.  Run after pre_filter; tcount is taken from its touched total.
-__device__ void pre_grow_request(const GraphCtx &g, unsigned long long *sh) {
+// Step A2 (insert): tables whose load would pass load_num/load_den must grow:
+// list them (M[0] = {x, new size}) and total their sizes.  Run after pre_filter;
+// tcount is taken from its touched total.
+template <class Team>
+__device__ void pre_grow_request(Team &T, const GraphCtx &g, unsigned long long *sh) {
     const int32_t tc = (int32_t)g.ctl->ttotal;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl->tcount = tc;
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < tc; b0 += stride) {
+    const int64_t stride = (int64_t)T.nblocks() * blockDim.x;
+    if (T.leader()) g.ctl->tcount = tc;
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < tc; b0 += stride) {
         const int64_t i = b0 + threadIdx.x;
         bool grow = false;
         int32_t x = 0, nc = 0;
@@ -775,12 +521,12 @@ __device__ void pre_grow_request(const GraphCtx &g, unsigned long long *sh) {
     }
 }
 
-// The pool check before any table moves (split): every thread reads the same pool
-// top, since nothing is taken from the pool in this kernel.  When the pool cannot
+// The pool check before any table moves: every thread reads the same pool top,
+// since nothing is taken from the pool in this step.  When the pool cannot
 // take the growing tables, the batch's incoming counts are undone and the host
 // grows the pool and runs the batch again.
-__device__ void pre_pool_check(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_pool_check(Team &T, const GraphCtx &g) {
     const unsigned long long top = *g.pool_top;
     if (top + g.ctl->grow_total <= (unsigned long long)g.pool_cap) {
         if (T.leader()) g.ctl->pool_old = top;  // the new tables will fill [top, top + grow_total)
@@ -790,15 +536,16 @@ __device__ void pre_pool_check(const GraphCtx &g) {
     if (T.leader()) atomicOr(&g.ctl->err, kErrNeedPool);
 }
 
-// Room in the pool for every growing table (split, after the check), and the
+// Room in the pool for every growing table (after the check), and the
 // work list of the move: every old table cut into chunks of kGrowChunk slots,
 // items {growing-table index, chunk} in CL[0].  The rooms are contiguous from the
 // pool top read by the check.
 constexpr int kGrowChunk = 512;
 
-__device__ void pre_alloc(const GraphCtx &g, unsigned long long *sh) {
-    const int64_t gc = (int64_t)g.ctl->gtotal, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < gc; b0 += stride) {
+template <class Team>
+__device__ void pre_alloc(Team &T, const GraphCtx &g, unsigned long long *sh) {
+    const int64_t gc = (int64_t)g.ctl->gtotal, stride = (int64_t)T.nblocks() * blockDim.x;
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < gc; b0 += stride) {
         const int64_t i = b0 + threadIdx.x;
         const int4 it = i < gc ? g.M[0][i] : make_int4(0, 0, 0, 0);
         const unsigned long long off =
@@ -816,8 +563,8 @@ __device__ void pre_alloc(const GraphCtx &g, unsigned long long *sh) {
 }
 
 // Every new table starts empty: one fill of the contiguous rooms.
-__device__ void pre_clear(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_clear(Team &T, const GraphCtx &g) {
     int4 *p = reinterpret_cast<int4 *>(g.slots + g.ctl->pool_old);
     const int64_t n4 = (int64_t)(g.ctl->grow_total >> 2);
     for (int64_t j = T.tid(); j < n4; j += T.nthreads()) p[j] = empty4();
@@ -826,8 +573,8 @@ __device__ void pre_clear(const GraphCtx &g) {
 // The old entries go into the new tables, one warp per chunk of an old table (a
 // hub's table is spread over many warps).  The vertices still point at their old
 // tables; pre_commit repoints them afterwards.
-__device__ void pre_grow(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_grow(Team &T, const GraphCtx &g) {
     const int64_t nc_items = (int64_t)g.ctl->ctotal;
     for (int64_t c = T.wid(); c < nc_items; c += T.nwarps()) {
         const int4 ci = g.CL[0][c];
@@ -847,8 +594,8 @@ __device__ void pre_grow(const GraphCtx &g) {
 }
 
 // Every growing vertex points at its new table.
-__device__ void pre_commit(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_commit(Team &T, const GraphCtx &g) {
     const int64_t gc = (int64_t)g.ctl->gtotal;
     for (int64_t i = T.tid(); i < gc; i += T.nthreads()) {
         const int4 it = g.M[0][i];
@@ -863,16 +610,17 @@ __device__ __forceinline__ void shrink_item(const GraphCtx &g, int list, unsigne
     else report(g, kErrListOverflow, 24, j, k, list);
 }
 
-// Shrink plan (split, after the deletions): tables that became sparse or full of
+// Shrink plan (after the deletions): tables that became sparse or full of
 // tombstones get arena room for their live keys and go to the warp list (M[0])
 // or, above block_cap slots, the large list (M[1]) as {x, new size, arena base,
 // live keys}, whose rebuild is cut into chunks; speed only, skipped when the
 // arena is full.
-__device__ void pre_shrink_plan(const GraphCtx &g, unsigned long long *sh) {
+template <class Team>
+__device__ void pre_shrink_plan(Team &T, const GraphCtx &g, unsigned long long *sh) {
     const int32_t tc = (int32_t)g.ctl->ttotal;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) g.ctl->tcount = tc;
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < tc; b0 += stride) {
+    const int64_t stride = (int64_t)T.nblocks() * blockDim.x;
+    if (T.leader()) g.ctl->tcount = tc;
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < tc; b0 += stride) {
         const int64_t i = b0 + threadIdx.x;
         int32_t x = 0, nc = 0, d = 0, c = 0;
         bool want = false;
@@ -913,8 +661,8 @@ __device__ void pre_shrink_plan(const GraphCtx &g, unsigned long long *sh) {
 
 // Shrink, first pass: the small tables rebuilt whole, one warp each; the large
 // tables' live keys copied into their arena room, one warp per chunk of slots.
-__device__ void pre_shrink_a(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_shrink_a(Team &T, const GraphCtx &g) {
     const int32_t sc = (int32_t)g.ctl->gtotal;
     for (int i = T.wid(); i < sc; i += T.nwarps()) {
         const int4 it = g.M[0][i];
@@ -954,8 +702,8 @@ __device__ void pre_shrink_a(const GraphCtx &g) {
 // Shrink, second pass: a large table whose copy holds exactly its live keys is
 // cleared (its first nc slots) and takes its new size; otherwise it is reported
 // and kept.
-__device__ void pre_shrink_b(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_shrink_b(Team &T, const GraphCtx &g) {
     const int64_t n1 = (int64_t)g.ctl->c1total;
     for (int64_t c = T.wid(); c < n1; c += T.nwarps()) {
         const int4 ci = g.CL[1][c];
@@ -976,8 +724,8 @@ __device__ void pre_shrink_b(const GraphCtx &g) {
 
 // Shrink, third pass: the copied keys go back into the cleared tables, one warp
 // per chunk of keys.
-__device__ void pre_shrink_c(const GraphCtx &g) {
-    FreeTeam T;
+template <class Team>
+__device__ void pre_shrink_c(Team &T, const GraphCtx &g) {
     const int64_t n2 = (int64_t)g.ctl->c2total;
     for (int64_t c = T.wid(); c < n2; c += T.nwarps()) {
         const int4 ci = g.CL[2][c];
@@ -2161,8 +1909,8 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
 // entry in P[q] unless it equals the vertex's current pending level; results at
 // or below lmin contradict the level lemma and are reported.  A pending vertex
 // whose slack has not gone below 0 since its last evaluation would get the same
-// answer again: that evaluation is counted (as the oracle counts it) without the
-// scan.
+// answer again: that evaluation is counted (Algorithm 3 counts every evaluation)
+// without the scan.
 template <class Team>
 __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t count, int q, int32_t lmin,
                          const int32_t *sh_dnmin, int32_t *whist, int32_t *bhist, unsigned long long &evals,
@@ -2903,6 +2651,7 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
     int32_t *sh_upmax = sh;
     int32_t *sh_dnmin = sh + kMaxGroups;
     int *sh_scan = sh + 2 * kMaxGroups;  // 64 ints
+    unsigned long long *sh_res = reinterpret_cast<unsigned long long *>(sh_scan);  // block_reserve: <= 17 slots
     int32_t *sh_block = sh + 2 * kMaxGroups + 64;  // kWarpHist + 32 ints, block-wide desire-levels
     int32_t *whist = sh_block + kWarpHist + 32 + (threadIdx.x >> 5) * kWarpHist;
     int32_t *sh_stage = sh_block + kWarpHist + 32 + (blockDim.x >> 5) * kWarpHist;
@@ -2926,27 +2675,27 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
     if constexpr (kRoundsOnly) {  // a step kernel that failed stops the rounds too
         if (ld_volatile(&g.ctl->err)) return;
     } else if (in.B > 0) {
-        step_canonicalise(T, g, in);
+        pre_canon(T, g, in, sh_res);
         if (!T.sync()) return;  // ids outside [0,n): nothing has changed
         if (tr) tmark[nmark++] = global_ns();
-        step_filter(T, g, in);
+        pre_filter(T, g, in, sh_res);
         if (!T.sync()) return;
         if (tr) tmark[nmark++] = global_ns();
     }
     if (in.op == kOpInsert) {
         if constexpr (!kRoundsOnly) {
-            step_grow_request(T, g);
+            pre_grow_request(T, g, sh_res);
             if (!T.sync()) return;
-            if (T.leader() && *g.pool_top + g.ctl->grow_total > (unsigned long long)g.pool_cap)
-                atomicOr(&g.ctl->err, kErrNeedPool);  // host grows the pool and runs the batch again
-            if (!T.sync()) {
-                // nothing but the batch's incoming counts has changed: undo them for the rerun
-                if (ld_volatile(&g.ctl->err) == kErrNeedPool)
-                    for (int i = T.tid(); i < g.ctl->tcount; i += T.nthreads()) g.inc[g.touched[i]] = 0;
-                return;
-            }
+            pre_pool_check(T, g);  // on a full pool: the incoming counts undone, kErrNeedPool
+            if (!T.sync()) return;  // the host grows the pool and runs the batch again
             if (tr) tmark[nmark++] = global_ns();
-            if (!step_grow_apply(T, g)) return;
+            pre_alloc(T, g, sh_res);
+            if (!T.sync()) return;
+            pre_clear(T, g);
+            if (!T.sync()) return;
+            pre_grow(T, g);
+            if (!T.sync()) return;
+            pre_commit(T, g);
             if (!T.sync()) return;
             if (tr) tmark[nmark++] = global_ns();
             step_apply_insert(T, g);
@@ -2969,7 +2718,13 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
             step_apply_delete(T, g);
             if (!T.sync()) return;
             if (tr) tmark[nmark++] = global_ns();
-            step_shrink(T, g, sh_scan);
+            pre_shrink_plan(T, g, sh_res);
+            if (!T.sync()) return;
+            pre_shrink_a(T, g);
+            if (!T.sync()) return;
+            pre_shrink_b(T, g);
+            if (!T.sync()) return;
+            pre_shrink_c(T, g);
             if (!T.sync()) return;
             if (tr) tmark[nmark++] = global_ns();
         }

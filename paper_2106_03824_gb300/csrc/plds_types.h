@@ -42,7 +42,6 @@ struct Ctl {
     unsigned long long ucount;   // unique canonical keys
     unsigned long long vcount;   // valid (applied) keys
     int32_t tcount;              // touched vertices
-    int32_t shrink_used;         // arena ints used by table shrinking
     unsigned long long grow_total;  // slots requested by growing tables
     unsigned long long ltop[3];  // insertion: int4 units handed out of each up-list buffer
     int32_t imcnt[3];     // insertion: movers marked for a phase (phase index mod 3)
@@ -87,7 +86,7 @@ struct Ctl {
     int32_t err_info[3];  // values seen by that check (diagnostics)
     int32_t trace_n;      // per-round records written
     int32_t rbcnt;        // violators with large tables (block-wide desire-level)
-    // split path (steps as separate kernels): list lengths reserved per block
+    // steps before the rounds: list lengths and room reserved once per block
     unsigned long long ttotal;  // touched vertices
     unsigned long long gtotal;  // growing tables (insert) / warp shrink list (delete)
     unsigned long long btotal;  // block shrink list
