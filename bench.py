@@ -51,9 +51,13 @@ UNIT = "updates/s"
 # dram bytes / executed algorithmic bytes of the batch kernel, from the ncu capture
 # summarised in profiles/ (kernel source hash at capture time); traffic is
 # reported as null when the kernel source has changed since.
-NCU_TRAFFIC = {"kernel_sha": "7c622e60a125de01", "dram_per_algo_byte": 1.0005,
-               "capture": "ncu DRAM counters of three k_batch_grid launches of the R-MAT 20 step stream "
-                          "(profiles/k_batch_grid_traffic_rmat20_B1e6.md)"}
+# DRAM bytes per algorithmic byte, from an ncu counter capture of the timed steps'
+# kernels (profiles/traffic_rmat20_B1e6.md); valid only for the kernel sources it was
+# taken on (kernel_sha), otherwise `traffic` is reported as null.
+NCU_TRAFFIC = {"kernel_sha": "3e23687c2e486c55", "rounds_dram_per_algo_byte": 0.671,
+               "batch_dram_per_algo_byte": 2.152,
+               "capture": "ncu DRAM counters of every kernel of the timed steps of the R-MAT 20 stream, "
+                          "Ins 14-15 and Del 0-1 (profiles/traffic_rmat20_B1e6.md)"}
 
 
 def kernel_sha() -> str:
@@ -111,6 +115,13 @@ def algo_bytes_survey(s: dict) -> int:
     per valid update 64 B; per submitted edge 8 B.  Executed rounds only."""
     return (8 * s["submitted"] + 64 * s["valid"] + 4 * (s["moves"] - s["skipped_moves"])
             + 8 * (s["visits"] - s["skipped_visits"]) + 8 * s["affected"] + 8 * s["dl_visits"])
+
+
+def algo_bytes_steps(s: dict) -> int:
+    """The part of algo_bytes that the step kernels before the level rounds do: 8 B
+    per submitted edge, 64 B per applied update.  The rest (level writes, neighbour
+    examinations, desire-level scans) is the rounds kernel's."""
+    return 8 * s["submitted"] + 64 * s["valid"]
 
 
 def algo_bytes_with_skipped(s: dict, kind: str) -> int:
@@ -551,22 +562,76 @@ def device_checks(P, g, n, present, tables):
             "invariant2": bool((ups[pos] >= dnmin[(lv[pos] - 1) // Lg]).all())}
 
 
+def unique_edges_device(pairs):
+    """Distinct non-loop edges of a device pair list, canonical (u < v), int32 [k, 2]."""
+    import torch
+    keys = []
+    for s0 in range(0, pairs.shape[0], 1 << 27):
+        u = pairs[s0:s0 + (1 << 27), 0].long()
+        v = pairs[s0:s0 + (1 << 27), 1].long()
+        keep = u != v
+        u, v = u[keep], v[keep]
+        keys.append(torch.minimum(u, v) * (1 << 32) + torch.maximum(u, v))
+    k = torch.unique(torch.cat(keys))
+    del keys
+    return torch.stack([(k >> 32).int(), (k & 0xFFFFFFFF).int()], 1).contiguous()
+
+
+def large_parity(P, gen, n, B, nb, gold_path):
+    """The first nb batches of the large insertion stream on a fresh handle, each
+    batch's level and counter digests against the oracle's (written by
+    tests/golden/make_large_digests.py from oracle/ only).  Untimed."""
+    import torch
+    if not gold_path.exists():
+        return {"checked": 0, "note": f"{gold_path.name} not present"}
+    gold = json.loads(gold_path.read_text())
+    recs = gold.get("ins", [])[:nb]
+    if gold["n"] != n or gold["batch"] != B or gold["perm_sha256"] != sha_i32(gen.perm):
+        return {"checked": 0, "note": "the golden file describes another stream"}
+    g = P.PLDS(n)
+    ok_lv = ok_ct = ok_n = True
+    for j, r in enumerate(recs):
+        b = gen.draws_torch(r["start"], r["size"])
+        g.insert(b)
+        st = g.stats()
+        d, u, s_ = g.counters()
+        ok_lv &= sha_i32(g.levels()) == r["levels"]
+        ok_ct &= sha_i32(d, u, s_) == r["counters"]
+        ok_n &= all(st[k] == r[k] for k in ("valid", "rounds", "moves", "visits"))
+        del b
+    g.close()
+    torch.cuda.empty_cache()
+    return {"checked": len(recs), "updates": sum(r["size"] for r in recs), "levels_equal": bool(ok_lv),
+            "counters_equal": bool(ok_ct), "work_counts_equal": bool(ok_n),
+            "against": "oracle digests after every batch (" + gold_path.name + ")"}
+
+
+def sha_i32(*arrays) -> str:
+    h = hashlib.sha256()
+    for x in arrays:
+        h.update(np.ascontiguousarray(x, dtype="<i4").tobytes())
+    return h.hexdigest()
+
+
 def run_large(args):
     """The large configuration: a Chung-Lu graph shaped like a billion-edge social
-    graph (n = 41.7M, ~1.2B edges, exponent 2.1) and a 24M-vertex road-like grid,
-    plain form, device-resident inputs; Ins / Mix / Del protocols at batches of 1e7
-    and 1e6, device-side property checks on the loaded graph."""
+    graph (n = 41.7M, 1.2B drawn pairs, exponent 2.1; counter-based draws made on the
+    device) and a 24M-vertex road-like grid, plain form, device-resident inputs; Ins /
+    Mix / Del protocols at batches of 1e7 and 1e6, device-side property checks on the
+    loaded graph, and the first 10^8 insertions checked against the oracle's digests."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2106_03824_gb300 import plds as P
     torch.cuda.set_device(0)
     n, m = args.large_n, args.large_m
+    B7, B6 = 10_000_000, 1_000_000
     t0 = time.perf_counter()
-    e = W.shuffled_device(W.chung_lu_device(n, m, 2.1, seed=1), 11)
+    gen = W.ChungLuDraws(n, m, 2.1, seed=1)
+    raw = gen.draws_torch(0, m)  # the insertion stream: raw pairs in draw order
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    m = int(e.shape[0])
+    parity = large_parity(P, gen, n, B7, 10, ROOT / "tests" / "golden" / "chunglu41m_first1e8_digests.json")
 
     def timed(calls):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
@@ -585,22 +650,31 @@ def run_large(args):
     out = {}
     g = P.PLDS(n)
     k = int(0.9 * m)
-    B7, B6 = 10_000_000, 1_000_000
-    # build: the first 90 % in batches of 1e7 (the Ins protocol at 1e7)
-    out["ins_1e7"] = timed([(g.insert, e[s:min(s + B7, k)]) for s in range(0, k, B7)])
+    # build: the first 90 % of the draws in batches of 1e7 (the Ins protocol at 1e7)
+    out["ins_1e7"] = timed([(g.insert, raw[s:min(s + B7, k)]) for s in range(0, k, B7)])
     st = g.stats()
-    out["loaded"] = {"edges": k, "device_bytes": st["device_bytes"], "pool_slots": st["pool_slots_cap"]}
-    out["checks_loaded"] = device_checks(P, g, n, e[:k], g.tables())
-    # Mix on the 90 %-loaded graph: insert from the absent 10 %, delete from a shuffled present pool
-    present = W.shuffled_device(e[:k], 12)
-    ai, pi = k, 0
+    present = unique_edges_device(raw[:k])
+    out["loaded"] = {"draws": k, "edges": int(present.shape[0]), "device_bytes": st["device_bytes"],
+                     "pool_slots": st["pool_slots_cap"]}
+    out["checks_loaded"] = device_checks(P, g, n, present, g.tables())
+    # Mix on the 90 %-loaded graph: insert edges of the last 10 % of the draws that are
+    # not present yet, delete from a shuffled present pool
+    later = unique_edges_device(raw[k:])
+    del raw
+    pk = present[:, 0].long() * (1 << 32) + present[:, 1].long()
+    lk = later[:, 0].long() * (1 << 32) + later[:, 1].long()
+    pos = torch.searchsorted(pk, lk).clamp_(max=pk.numel() - 1)
+    absent = W.shuffled_device(later[pk[pos] != lk], 13)
+    del pk, lk, pos, later
+    present = W.shuffled_device(present, 12)
+    ai, pi = 0, 0
 
     def mixed(B, count):
         nonlocal ai, pi
         calls = []
         for _ in range(count):
             h = B // 2
-            calls.append((g.insert, e[ai:ai + h]))
+            calls.append((g.insert, absent[ai:ai + h]))
             calls.append((g.delete, present[pi:pi + h]))
             ai += h
             pi += h
@@ -608,16 +682,16 @@ def run_large(args):
 
     out["mix_1e7"] = timed(mixed(B7, 3))
     out["mix_1e6"] = timed(mixed(B6, 10))
-    out["ins_1e6"] = timed([(g.insert, e[ai + j * B6:ai + (j + 1) * B6]) for j in range(5)])
+    out["ins_1e6"] = timed([(g.insert, absent[ai + j * B6:ai + (j + 1) * B6]) for j in range(5)])
     ai += 5 * B6
     out["del_1e6"] = timed([(g.delete, present[pi + j * B6:pi + (j + 1) * B6]) for j in range(5)])
     pi += 5 * B6
     # Del at 1e7: everything still present
-    rest = torch.cat([present[pi:], e[k:ai]])
+    rest = torch.cat([present[pi:], absent[:ai]])
     out["del_1e7"] = timed([(g.delete, rest[s:s + B7]) for s in range(0, rest.shape[0], B7)])
     out["empty_after_del"] = bool(int(g.levels().max()) == 0 and int(g.counters()[0].max()) == 0)
     g.close()
-    del e, present, rest
+    del present, absent, rest
     torch.cuda.empty_cache()
     # the road-like contrast: 24M-vertex grid, degree <= 4 plus 10 % diagonals
     side = args.grid_side
@@ -634,10 +708,11 @@ def run_large(args):
     line = {"metric": "edge updates/s, large graphs (plain form)", "value": out["ins_1e7"]["updates_per_s"],
             "unit": UNIT, "n_gpus": 1, "steps": out["ins_1e7"]["batches"], "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "form": "large",
-            "config": {"workload": f"Chung-Lu n={n}, m={m}, exponent 2.1 (generated on the device, "
-                                   f"{t_gen:.1f} s); grid {side}x{side} with 10% diagonals",
-                       "value_is": "Ins protocol at batch 1e7 while loading 90% of the edges"},
-            "chung_lu": out, "grid": grid}
+            "config": {"workload": f"Chung-Lu n={n}, {m} drawn pairs, exponent 2.1 (counter-based draws "
+                                   f"made on the device, {t_gen:.1f} s); grid {side}x{side} with 10% diagonals",
+                       "value_is": "Ins protocol at batch 1e7 while loading 90% of the draws (raw pairs: "
+                                   "repeats and self-loops included, dropped by the batch rules)"},
+            "parity_first_1e8": parity, "chung_lu": out, "grid": grid}
     print(json.dumps(line), flush=True)
 
 
@@ -969,10 +1044,12 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     host_lat = []
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets an ncu capture select the timed steps' kernels
         ev0.record()
         upd, recs = run_steps(g, args.warmup, args.steps, lat=host_lat)
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
@@ -983,33 +1060,62 @@ def main():
     t_max = t_max_s * 1e3
     value = upd_all / t_max_s
 
-    # roofline of the batch kernel: algorithmic bytes of the executed work / event-timed kernel duration
+    # roofline: algorithmic bytes of the executed work / event-timed duration, for the
+    # level-rounds kernel (the dominant one) and for the whole launch sequence of a batch
+    # (step kernels + rounds kernel); both measured on the handle's stream
+    nb = len(recs)
     kern_ns = sum(r["kernel_ns"] for _, r in recs)
+    pre_ns = sum(r["pre_ns"] for _, r in recs)
+    rnd_ns = kern_ns - pre_ns
     abytes = sum(algo_bytes(r, kind) for kind, r in recs)
+    pbytes = sum(algo_bytes_steps(r) for _, r in recs)
     sbytes = sum(algo_bytes_survey(r) for _, r in recs)
     xbytes = sum(algo_bytes_with_skipped(r, kind) for kind, r in recs)
-    achieved = abytes / (kern_ns / 1e9) / 1e9 if kern_ns else None
-    s_achieved = sbytes / (kern_ns / 1e9) / 1e9 if kern_ns else None
     peak, peak_src = measured_peaks()
-    traffic = None
-    if NCU_TRAFFIC["kernel_sha"] == kernel_sha() and NCU_TRAFFIC["dram_per_algo_byte"]:
-        traffic = NCU_TRAFFIC["dram_per_algo_byte"] * abytes / len(recs)
-    if args.dump_recs:  # per timed step: the batch kernel's algorithmic bytes (matches ncu launch lists)
+
+    def gbs(b, ns):
+        return b / (ns / 1e9) / 1e9 if ns > 0 else None
+
+    def frac(a):
+        return a / peak if a else None
+
+    cur = NCU_TRAFFIC["kernel_sha"] == kernel_sha()
+    r_traffic = (NCU_TRAFFIC["rounds_dram_per_algo_byte"] * (abytes - pbytes) / nb
+                 if cur and NCU_TRAFFIC["rounds_dram_per_algo_byte"] else None)
+    b_traffic = (NCU_TRAFFIC["batch_dram_per_algo_byte"] * abytes / nb
+                 if cur and NCU_TRAFFIC["batch_dram_per_algo_byte"] else None)
+    if args.dump_recs:  # per timed step: algorithmic bytes and durations (matches ncu launch lists)
         with open(args.dump_recs, "w") as f:
-            json.dump([{"kind": kind, "algo_bytes": algo_bytes(r, kind), "algo_bytes_survey": algo_bytes_survey(r),
-                        "kernel_ns": r["kernel_ns"], "launches": r["launches"], "valid": r["valid"]}
+            json.dump([{"kind": kind, "algo_bytes": algo_bytes(r, kind), "algo_bytes_steps": algo_bytes_steps(r),
+                        "algo_bytes_survey": algo_bytes_survey(r), "kernel_ns": r["kernel_ns"],
+                        "pre_ns": r["pre_ns"], "launches": r["launches"], "valid": r["valid"]}
                        for kind, r in recs], f)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_batch_grid", "peak_source": peak_src,
-            "kernel_ms_per_launch": kern_ns / 1e6 / len(recs),
-            "algo_bytes_per_launch": abytes / len(recs),
-            "definition": "executed work, insertion moves at their up-degree (up-neighbours examined)",
-            "survey_definition": {"algo_bytes_per_launch": sbytes / len(recs), "achieved": s_achieved,
-                                  "frac": (s_achieved / peak) if s_achieved else None,
+    a_rnd = gbs(abytes - pbytes, rnd_ns)
+    s_rnd = gbs(sbytes - pbytes, rnd_ns)
+    a_seq = gbs(abytes, kern_ns)
+    s_seq = gbs(sbytes, kern_ns)
+    a_pre = gbs(pbytes, pre_ns)
+    roof = {"bound": "hbm", "achieved": a_rnd, "peak": peak, "unit": "GB/s", "frac": frac(a_rnd),
+            "traffic": r_traffic, "kernel": "k_batch_grid", "peak_source": peak_src,
+            "kernel_ms_per_launch": rnd_ns / 1e6 / nb,
+            "algo_bytes_per_launch": (abytes - pbytes) / nb,
+            "definition": "executed work of the level rounds: 4 B per level change, 8 B per neighbour "
+                          "examined (insertion moves: up-neighbours; deletion moves: all), 8 B per neighbour "
+                          "read by a desire-level evaluation; skipped pure rounds left out",
+            "survey_definition": {"algo_bytes_per_launch": (sbytes - pbytes) / nb, "achieved": s_rnd,
+                                  "frac": frac(s_rnd),
                                   "definition": "executed work, every move at its degree + 8 B per affected "
                                                 "neighbour"},
-            "with_skipped_rounds": {"algo_bytes_per_launch": xbytes / len(recs),
+            "batch_sequence": {"kernels": "step kernels (9 per insertion batch, 7 per deletion batch) "
+                                          "+ k_batch_grid, one batch call",
+                               "ms_per_batch": kern_ns / 1e6 / nb, "algo_bytes_per_batch": abytes / nb,
+                               "achieved": a_seq, "frac": frac(a_seq), "traffic": b_traffic,
+                               "survey_algo_bytes_per_batch": sbytes / nb, "survey_achieved": s_seq,
+                               "survey_frac": frac(s_seq)},
+            "step_kernels": {"ms_per_batch": pre_ns / 1e6 / nb, "algo_bytes_per_batch": pbytes / nb,
+                             "achieved": a_pre, "frac": frac(a_pre),
+                             "definition": "8 B per submitted edge + 64 B per applied update"},
+            "with_skipped_rounds": {"algo_bytes_per_batch": xbytes / nb,
                                     "note": "the skipped pure rounds counted as Algorithm 2 would run them; "
                                             "not a bandwidth figure"}}
 

@@ -196,19 +196,42 @@ __device__ __forceinline__ bool table_find(const int32_t *slots, int64_t off, in
 }
 
 // Insert a key known to be absent; returns 1 if a tombstone was reused, 0 if an
-// empty slot, -1 if the table is full (cannot happen under the load bound).
+// empty slot, -1 if the table is full (cannot happen under the load bound).  One
+// 16-byte load per probed group, then a compare-and-swap on each free slot it
+// showed (other threads may be inserting into the same table).
 __device__ __forceinline__ int table_insert(int32_t *slots, int64_t off, int32_t cap, int32_t key) {
     int32_t *t = slots + off;
     uint32_t ng = (uint32_t)cap >> 2, gi = home_group(key, cap);
     for (uint32_t it = 0; it < ng; ++it) {
+        const int4 q = __ldcg(reinterpret_cast<const int4 *>(t) + gi);
+        const int32_t qs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
         for (int s = 0; s < 4; ++s) {
-            int32_t *p = t + gi * 4 + s;
-            int32_t cur = *(volatile int32_t *)p;
+            int32_t cur = qs[s];
             while (cur == kEmpty || cur == kTomb) {
-                int32_t old = atomicCAS(p, cur, key);
+                const int32_t old = atomicCAS(t + gi * 4 + s, cur, key);
                 if (old == cur) return cur == kTomb ? 1 : 0;
                 cur = old;
             }
+        }
+        gi = (gi + 1) & (ng - 1);
+    }
+    return -1;
+}
+
+// Insert into a table being rebuilt (no tombstones: every slot is EMPTY or a key):
+// compare-and-swap straight away, from a slot of the home group picked by the key
+// so that keys sharing a group rarely race for one slot.  Any free slot of the
+// first group with room is as good as another for table_find.
+__device__ __forceinline__ int table_insert_fresh(int32_t *slots, int64_t off, int32_t cap, int32_t key) {
+    int32_t *t = slots + off;
+    const uint32_t ng = (uint32_t)cap >> 2;
+    uint32_t gi = home_group(key, cap);
+    const int s0 = (int)(((uint32_t)key * 0x2545F491u) >> 30);
+    for (uint32_t it = 0; it < ng; ++it) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (atomicCAS(t + gi * 4 + ((s0 + k) & 3), kEmpty, key) == kEmpty) return 0;
         }
         gi = (gi + 1) & (ng - 1);
     }
@@ -376,7 +399,7 @@ __device__ __forceinline__ void shrink_table_warp(const GraphCtx &g, int32_t sx,
     for (int j = lane_id(); j < (snc >> 2); j += 32) t4[j] = empty4();
     __syncwarp();
     __threadfence_block();
-    for (int j = lane_id(); j < written; j += 32) table_insert(g.slots, off, snc, ar[j]);
+    for (int j = lane_id(); j < written; j += 32) table_insert_fresh(g.slots, off, snc, ar[j]);
     __syncwarp();
     if (lane_id() == 0) {
         g.cap[sx] = snc;
@@ -585,10 +608,10 @@ __device__ void pre_grow(Team &T, const GraphCtx &g) {
         const int j_end = min(oc, (ci.y + 1) * kGrowChunk) >> 2;
         for (int j = (ci.y * kGrowChunk >> 2) + lane_id(); j < j_end; j += 32) {
             const int4 q = ot[j];
-            if (q.x >= 0) table_insert(g.slots, noff, it.y, q.x);
-            if (q.y >= 0) table_insert(g.slots, noff, it.y, q.y);
-            if (q.z >= 0) table_insert(g.slots, noff, it.y, q.z);
-            if (q.w >= 0) table_insert(g.slots, noff, it.y, q.w);
+            if (q.x >= 0) table_insert_fresh(g.slots, noff, it.y, q.x);
+            if (q.y >= 0) table_insert_fresh(g.slots, noff, it.y, q.y);
+            if (q.z >= 0) table_insert_fresh(g.slots, noff, it.y, q.z);
+            if (q.w >= 0) table_insert_fresh(g.slots, noff, it.y, q.w);
         }
     }
 }
@@ -733,7 +756,8 @@ __device__ void pre_shrink_c(Team &T, const GraphCtx &g) {
         if (g.lfill[0][it.x] != it.w) continue;  // reported and kept in the second pass
         const int64_t off = g.off[it.x];
         const int k_end = min(it.w, (ci.y + 1) * kGrowChunk);
-        for (int k = ci.y * kGrowChunk + lane_id(); k < k_end; k += 32) table_insert(g.slots, off, it.y, g.arena[it.z + k]);
+        for (int k = ci.y * kGrowChunk + lane_id(); k < k_end; k += 32)
+            table_insert_fresh(g.slots, off, it.y, g.arena[it.z + k]);
     }
 }
 

@@ -257,6 +257,94 @@ def chung_lu_device(n: int, m: int, gamma: float, seed: int = 1, device: str = "
     return torch.stack([torch.minimum(a, b), torch.maximum(a, b)], 1).contiguous()
 
 
+# ---------------------------------------------------------------------------
+# Counter-based Chung-Lu draws: draw k is a pure function of (seed, k), computed in
+# int64 arithmetic whose every intermediate stays below 2^63, so numpy on the host
+# and torch on the device give identical edges.  Any slice of a billion-draw stream
+# can then be made on either side alone (the device generates the whole stream of
+# the large configuration; the host remakes its first batches for the oracle).
+# ---------------------------------------------------------------------------
+_P31 = 2_147_483_647  # 2^31 - 1, prime
+_H31_ROUNDS = ((16_807, 1), (1_583_458_089, 7), (784_588_716, 13), (1_222_560_079, 17))
+
+
+def _h31(x, seed: int):
+    """Integer hash of non-negative int64 counters x (numpy array or torch tensor)
+    to [0, 2^31 - 1): an affine map of (x mod p, x div p, seed) mod p, then four
+    rounds of multiply-add mod p and an xor-shift."""
+    lo = x % _P31
+    hi = x // _P31
+    y = (lo * 1_103_515_245 + (hi * 48_271) % _P31 + (int(seed) * 69_621 + 12_345) % _P31) % _P31
+    for a, b in _H31_ROUNDS:
+        y = (y * a + b) % _P31
+        y = y ^ (y >> 15)
+    return y
+
+
+class ChungLuDraws:
+    """The chung_lu model (same weights, scaling to mean degree 2m/n and truncation at
+    sqrt(2m)) as an indexed stream of i.i.d. endpoint pairs, with vertex ids randomly
+    permuted.  Draw k is (perm[u_k], perm[v_k]) with u_k, v_k drawn proportional to
+    the weights from four hashes of (seed, k); pairs come as drawn (either order,
+    self-loops and repeats included, as a raw update stream carries them).
+
+    The weights are quantised to int64 (total near 2^52) and cumulated on the host;
+    each endpoint is the first index whose cumulative weight exceeds a 62-bit hash
+    value reduced mod the total (exact integer searchsorted on either side)."""
+
+    def __init__(self, n: int, m: int, gamma: float, seed: int = 1):
+        if n < 2 or m <= 0:
+            raise ValueError("need n >= 2 and m > 0")
+        self.n, self.m, self.gamma, self.seed = int(n), int(m), float(gamma), int(seed)
+        w = np.arange(1, n + 1, dtype=np.float64) ** (-1.0 / (gamma - 1.0))
+        cap = np.sqrt(2.0 * m)
+        for _ in range(8):
+            w = np.minimum(w * (2.0 * m / w.sum()), cap)
+        q = np.floor(w * (float(1 << 52) / w.sum())).astype(np.int64)
+        del w
+        self.cw = np.cumsum(q)
+        self.total = int(self.cw[-1])
+        i = np.arange(n, dtype=np.int64)
+        self.perm = np.argsort(_h31(i, self.seed + 1) * (1 << 32) + i, kind="stable").astype(np.int32)
+        self._dev = {}
+
+    def _endpoints(self, k, xp_search, cw):
+        a = _h31(4 * k, self.seed)
+        b = _h31(4 * k + 1, self.seed)
+        c = _h31(4 * k + 2, self.seed)
+        d = _h31(4 * k + 3, self.seed)
+        ru = ((a << 31) | b) % self.total
+        rv = ((c << 31) | d) % self.total
+        return xp_search(cw, ru), xp_search(cw, rv)
+
+    def draws(self, start: int, count: int, chunk: int = 1 << 22) -> np.ndarray:
+        """Draws start .. start+count-1 as int32[count, 2] (host, numpy)."""
+        out = np.empty((count, 2), dtype=np.int32)
+        for s in range(0, count, chunk):
+            c = min(chunk, count - s)
+            k = np.arange(start + s, start + s + c, dtype=np.int64)
+            u, v = self._endpoints(k, lambda cw, r: np.searchsorted(cw, r, side="right"), self.cw)
+            out[s:s + c, 0] = self.perm[u]
+            out[s:s + c, 1] = self.perm[v]
+        return out
+
+    def draws_torch(self, start: int, count: int, device="cuda", chunk: int = 1 << 25):
+        """The same draws as a torch int32 [count, 2] tensor computed on `device`."""
+        import torch
+        dev = torch.device(device)
+        if dev not in self._dev:
+            self._dev[dev] = (torch.from_numpy(self.cw).to(dev), torch.from_numpy(self.perm).to(dev))
+        cw, perm = self._dev[dev]
+        out = torch.empty((count, 2), dtype=torch.int32, device=dev)
+        for s in range(0, count, chunk):
+            c = min(chunk, count - s)
+            k = torch.arange(start + s, start + s + c, dtype=torch.int64, device=dev)
+            u, v = self._endpoints(k, lambda t, r: torch.searchsorted(t, r, right=True), cw)
+            out[s:s + c, 0] = perm[u]
+            out[s:s + c, 1] = perm[v]
+        return out
+
+
 def shuffled_device(edges, seed: int):
     """A seeded permutation of a device edge tensor."""
     import torch

@@ -30,3 +30,10 @@ def test_with_skipped_rounds():
     assert bench.algo_bytes_with_skipped(S, "ins") == 8000 + 57600 + 2000 + 24000 + 480
     z = dict(S, skipped_moves=0, skipped_visits=0, skipped_up_visits=0)
     assert bench.algo_bytes_with_skipped(z, "ins") == bench.algo_bytes(z, "ins")
+
+
+def test_step_bytes_are_part_of_executed_bytes():
+    # the step kernels' share: 8 per submitted edge + 64 per applied update
+    assert bench.algo_bytes_steps(S) == 8000 + 57600
+    for kind in ("ins", "del"):
+        assert bench.algo_bytes(S, kind) - bench.algo_bytes_steps(S) > 0

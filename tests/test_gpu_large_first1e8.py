@@ -1,0 +1,65 @@
+"""Bit-exact parity on the first 10^8 updates of the large configuration (GPU).
+
+The large configuration loads a 41.7 M-vertex Chung-Lu graph (exponent 2.1) from a
+stream of 1.2 B counter-based endpoint draws (workloads.ChungLuDraws) in batches of
+10^7.  Its first ten batches, made on the device exactly as the benchmark makes
+them, must leave the level array, deg||up||up* and the batch's work counts equal to
+the sequential oracle's after every batch (SHA-256 digests in
+tests/golden/chunglu41m_first1e8_digests.json, written by make_large_digests.py
+from oracle/ only).  The same draws made on the host and on the device must agree
+first, or the comparison would be of two different streams.
+"""
+import hashlib
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2106_03824_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = Path(__file__).resolve().parent / "golden" / "chunglu41m_first1e8_digests.json"
+COUNTS = ("valid", "rounds", "moves", "visits", "dl_evals", "dl_visits")
+
+
+def digest(*arrays) -> str:
+    h = hashlib.sha256()
+    for a in arrays:
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    return h.hexdigest()
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_03824_gb300 import plds
+    return plds
+
+
+def test_first_1e8_insertions_match_oracle(P):
+    if not GOLD.exists():
+        pytest.skip(f"{GOLD.name} not written yet (make_large_digests.py)")
+    gold = json.loads(GOLD.read_text())
+    recs = gold["ins"]
+    assert len(recs) == 10 and sum(r["size"] for r in recs) == 10 ** 8
+    gen = W.ChungLuDraws(gold["n"], gold["m"], 2.1, seed=1)
+    assert digest(gen.perm) == gold["perm_sha256"]
+    assert hashlib.sha256(gen.cw.astype("<i8").tobytes()).hexdigest() == gold["cw_sha256"]
+    g = P.PLDS(gold["n"])
+    for j, r in enumerate(recs):
+        b = gen.draws_torch(r["start"], r["size"])
+        assert digest(b.cpu().numpy()) == r["draws"], f"batch {j}: device draws differ from the host's"
+        g.insert(b)
+        st = g.stats()
+        assert digest(g.levels()) == r["levels"], f"batch {j}: levels"
+        assert digest(*g.counters()) == r["counters"], f"batch {j}: counters"
+        for k in COUNTS:
+            assert st[k] == r[k], f"batch {j}: {k} {st[k]} != {r[k]}"
+        del b
+    g.close()
