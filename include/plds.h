@@ -92,7 +92,9 @@ typedef struct plds_stats {
 
 /* Tuning knobs: they change speed only, never results. Zero fields keep defaults. */
 typedef struct plds_tuning {
-    int32_t thread_max_cap;   /* tables up to this many slots are scanned by one thread */
+    int32_t thread_max_cap;   /* tables up to this many slots are scanned by one thread (0 = default:
+                                 8 for deletion batches and insertion batches of at most 300,000
+                                 edges, 16 for larger insertion batches and the serving loop) */
     int32_t load_num;         /* a table grows when live+tombstones+incoming > cap*load_num/load_den */
     int32_t load_den;
     int32_t block_threads;    /* threads per block of the batch kernel (multiple of 32, 128..512) */

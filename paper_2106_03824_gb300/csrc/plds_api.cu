@@ -465,6 +465,15 @@ static int grow_pool(plds *h, int64_t extra) {
     return cuda_check(h);
 }
 
+// Default thread cutoff of a batch (tuning field 0).  Measured on R-MAT scale 20
+// (Ins and Del protocols): 8 slots save 2-4 % on deletion batches and on insertion
+// batches of 10^5 edges, 16 slots save 3 % on insertion batches of 10^6.  The
+// serving loop's context (B = 0: batches of every size) keeps 16.
+static int32_t default_thread_cap(int32_t op, int64_t B) {
+    if (B <= 0) return 16;
+    return (op == kOpDelete || B <= 300000) ? 8 : 16;
+}
+
 static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     GraphCtx g{};
     g.n = h->n;
@@ -473,7 +482,7 @@ static GraphCtx make_ctx(plds *h, int32_t op, const int32_t *edges, int64_t B) {
     g.G = h->T.G;
     g.op = op;
     g.stamp_base = h->stamp_base;
-    g.thread_max_cap = h->tune.thread_max_cap > 0 ? h->tune.thread_max_cap : 16;
+    g.thread_max_cap = h->tune.thread_max_cap > 0 ? h->tune.thread_max_cap : default_thread_cap(op, B);
     g.load_num = h->tune.load_num > 0 ? h->tune.load_num : 3;
     g.load_den = h->tune.load_den > 0 ? h->tune.load_den : 4;
     g.block_cap = h->tune.block_cap > 0 ? h->tune.block_cap : 1024;

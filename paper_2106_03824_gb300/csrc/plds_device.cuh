@@ -43,6 +43,9 @@ struct GridTeam {
     __device__ int nwarps() const { return nthreads() >> 5; }
     __device__ int bid() const { return blockIdx.x; }
     __device__ int nblocks() const { return gridDim.x; }
+    // a warp's rank in work lists: consecutive ranks on different blocks (SMs), so
+    // that a short list spreads over the whole GPU instead of filling a few SMs
+    __device__ int srank() const { return (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
     // Grid-wide barrier with a bounded wait: a block that waits longer than
     // limit_ns (or sees the error word set) records kErrTimeout and leaves.
@@ -109,6 +112,7 @@ struct BlockTeam {
     __device__ int nwarps() const { return blockDim.x >> 5; }
     __device__ int bid() const { return 0; }
     __device__ int nblocks() const { return 1; }
+    __device__ int srank() const { return threadIdx.x >> 5; }
     __device__ bool leader() const { return threadIdx.x == 0; }
     __device__ bool sync() {
         __threadfence_block();
@@ -129,6 +133,7 @@ struct FreeTeam {
     __device__ int nwarps() const { return nthreads() >> 5; }
     __device__ int bid() const { return blockIdx.x; }
     __device__ int nblocks() const { return gridDim.x; }
+    __device__ int srank() const { return (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
 };
 
@@ -1281,7 +1286,7 @@ template <class Team>
 __device__ void ins_test_initial(Team &T, const GraphCtx &g, const RoundStage &st, int32_t s_lo, int32_t s_hi,
                                  int32_t L, int32_t cut, int32_t *wsm, int rot, int k1) {
     const int32_t fl = level_flag(L);
-    const int rank = (T.wid() + rot) % T.nwarps();
+    const int rank = (T.srank() + rot) % T.nwarps();
     for (int i0 = s_lo + rank * 32; i0 < s_hi; i0 += T.nwarps() * 32) {
         const int i = i0 + lane_id();
         bool mk = false;
@@ -1376,7 +1381,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             if (has_init)  // initial candidates on l + 1
                 ins_test_initial(T, g, st, s_lo, s_hi, l + 1, cut_next, wsm, T.nwarps() / 2, k + 1);
             // thread-mode movers: up to 4 groups (16 slots) per pass, loads issued together
-            for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
+            for (int i0 = T.srank() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
                 const int i = i0 + lane;
                 const int4 it = i < tlc ? g.TL[cur][i] : make_int4(0, 0, 0, 0);
                 const bool have = i < tlc && item_ok(g, it, it.y);
@@ -1413,7 +1418,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             // chunk items: four per warp iteration, all loads of a step issued together;
             // taken from the last warp down, so that in a small round the warps
             // scanning thread-mode items and those scanning chunks are different ones
-            const int crank = T.nwarps() - 1 - T.wid();
+            const int crank = T.nwarps() - 1 - T.srank();
             const int4 *lin4 = reinterpret_cast<const int4 *>(lin);
             for (int c0 = crank; c0 < clc; c0 += 4 * T.nwarps()) {
                 int4 it[4];
@@ -1572,7 +1577,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             passed = T.sync_fetch(
                 [&](int ln) {
                     if (ln < (int)(blockDim.x >> 5)) {  // warp ln of the block: its first chunk item
-                        const int cr = T.nwarps() - 1 - (T.wid() + ln);
+                        const int cr = T.nwarps() - 1 - (ln * T.nblocks() + T.bid());  // warp ln's srank
                         st.ph4[ln] = cr < g.clcap ? cl_next[cr] : make_int4(0, 0, 0, 0);
                     } else if (ln == 16) {
                         st.phs[1] = g.ctl->imcnt[nxt];
@@ -1941,7 +1946,7 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
                          unsigned long long &evisits) {
     const int lane = lane_id();
     int32_t *RL = g.R[1];
-    for (int i0 = T.wid() * 32; i0 < count; i0 += T.nwarps() * 32) {
+    for (int i0 = T.srank() * 32; i0 < count; i0 += T.nwarps() * 32) {
         const int i = i0 + lane;
         bool viol = false, big = false;
         int32_t w = 0;
@@ -1963,7 +1968,7 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
     }
     if (!T.sync()) return false;
     const int32_t nw = g.ctl->rcnt[1], nb = g.ctl->rbcnt;
-    for (int i = T.wid(); i < nw; i += T.nwarps()) {
+    for (int i = T.srank(); i < nw; i += T.nwarps()) {
         const int32_t w = RL[i], lw = g.level[w];
         int32_t sl;
         const int32_t d = warp_desire_level(g, w, lw, sh_dnmin, whist, &sl);
@@ -2069,7 +2074,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
         }
         // Phase 1: pending entries with dl == l move; the rest stay pending.
         const int32_t pc = g.ctl->pcnt[p];
-        for (int i0 = T.wid() * 32; i0 < pc; i0 += T.nwarps() * 32) {
+        for (int i0 = T.srank() * 32; i0 < pc; i0 += T.nwarps() * 32) {
             const int i = i0 + lane;
             bool mover = false, keep = false;
             int32_t v = 0, d = 0, pv = 0, c = 0;
@@ -2117,7 +2122,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
             g.ctl->nextmin[p] = kInf;
         }
         const int32_t tlc = g.ctl->tlcnt[0];
-        for (int i0 = T.wid() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
+        for (int i0 = T.srank() * 32; i0 < tlc; i0 += T.nwarps() * 32) {
             const int i = i0 + lane;
             const int4 it = i < tlc ? g.TL[0][i] : make_int4(0, 0, 0, 0);
             const int ng = (i < tlc && item_ok(g, it, it.y)) ? (1 << it.y) >> 2 : 0;
@@ -2161,7 +2166,7 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
             }
         }
         const int32_t clc = g.ctl->clcnt[0];
-        for (int c0 = T.wid(); c0 < clc; c0 += 4 * T.nwarps()) {
+        for (int c0 = T.srank(); c0 < clc; c0 += 4 * T.nwarps()) {
             int4 it[4];
             bool in[4];
             int32_t ws[16], lv[16];
