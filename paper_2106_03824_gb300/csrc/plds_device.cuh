@@ -1168,31 +1168,43 @@ __device__ bool ins_sort_candidates(Team &T, const GraphCtx &g, int *sh) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int32_t level_flag(int32_t l) { return (l & 1) ? kFlagOdd : kFlagEven; }
 
-// Effects of a mover of level l on its neighbour w (level word raw).  Returns bit 0
-// if w became a mover of level l + 1 here, bit 1 if w stays on level l + 1 or above
-// after the round (an entry of the mover's up-list for its next move), bit 2 if one
-// of w's counters changed (a neighbour the move affected).  Movers of
-// l read as flagged words on levels lmo .. l + 1 (lmo = l unless pure rounds were
-// just skipped); low gets the lowest level above l of a neighbour that is no mover.
-__device__ __forceinline__ int ins_effect(const GraphCtx &g, int32_t w, int32_t raw, int32_t l, int32_t lmo,
-                                          int32_t fcur, int32_t fnext, int32_t cut_next, int &cnt_l, int32_t &low) {
-    if (!valid_id(g, w)) return 0;  // empty slot or tombstone
-    const int32_t f = raw & kLevelMask;
-    if ((raw & fcur) && f >= lmo && f <= l + 1) return 2;  // a mover of level l as well
-    if (f == l) {
-        cnt_l++;
-        return 0;
+// Effects of a mover of level l on 16 neighbours ws (level words lv), in two
+// passes so that the counter atomics of all 16 are in flight together: first every
+// neighbour is classified and its counter updated -- a neighbour on l + 1 gains an
+// up-neighbour (returning add: the one add that sees the old value equal to the
+// cutoff marks it), one on l + 2 an up*-neighbour -- then the marks are set.
+// Per slot q: bit q of push if the neighbour became a mover of level l + 1 here,
+// of keep if it stays on level l + 1 or above after the round (an entry of the
+// mover's up-list for its next move); aff counts neighbours whose counters
+// changed; cnt4[q / 4] counts the neighbours left on l; low gets the lowest level
+// above l of a neighbour that is no mover.  Movers of l read as flagged words on
+// levels lmo .. l + 1 (lmo = l unless pure rounds were just skipped).
+__device__ __forceinline__ void ins_effects16(const GraphCtx &g, const int32_t (&ws)[16], const int32_t (&lv)[16],
+                                              int32_t l, int32_t lmo, int32_t fcur, int32_t fnext, int32_t cut_next,
+                                              int (&cnt4)[4], int32_t &low, unsigned &push, unsigned &keep,
+                                              unsigned &aff) {
+    int32_t old[16];
+    unsigned a1m = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int32_t w = ws[q], raw = lv[q], f = raw & kLevelMask;
+        const bool ok = valid_id(g, w);  // not an empty slot or a tombstone
+        const bool mov = ok && (raw & fcur) && f >= lmo && f <= l + 1;  // a mover of level l as well
+        const bool other = ok && !mov;
+        cnt4[q >> 2] += (other && f == l) ? 1 : 0;
+        const bool above = other && f > l;
+        if (above) low = min(low, f);
+        const bool a1 = above && f == l + 1, a2 = above && f == l + 2;
+        old[q] = 0;
+        if (a1) old[q] = atomicAdd(&g.up[w], 1);
+        if (a2) atomicAdd(&g.upstar[w], 1);
+        a1m |= a1 ? 1u << q : 0u;
+        keep |= (mov || above) ? 1u << q : 0u;
+        aff += (a1 || a2) ? 1u : 0u;
     }
-    if (f < l) return 0;
-    low = min(low, f);
-    if (f == l + 1) {
-        if (atomicAdd(&g.up[w], 1) == cut_next) return 6 | (!(atomicOr(&g.level[w], fnext) & fnext) ? 1 : 0);
-        return 6;
-    } else if (f == l + 2) {
-        atomicAdd(&g.upstar[w], 1);
-        return 6;
-    }
-    return 2;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (((a1m >> q) & 1u) && old[q] == cut_next && !(atomicOr(&g.level[ws[q]], fnext) & fnext)) push |= 1u << q;
 }
 
 // A mover of level l whose whole table has been scanned (total = its neighbours
@@ -1398,14 +1410,12 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                     }
 #pragma unroll
                     for (int q = 0; q < 16; ++q) lv[q] = valid_id(g, ws[q]) ? g.level[ws[q]] : 0;
-                    unsigned push = 0;
+                    unsigned push = 0, keep = 0;
+                    int c4[4] = {0, 0, 0, 0};
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        ideg += ws[q] >= 0;
-                        const int r = ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cnt_l, low);
-                        if (r & 1) push |= 1u << q;
-                        aff += (r >> 2) & 1;
-                    }
+                    for (int q = 0; q < 16; ++q) ideg += ws[q] >= 0;
+                    ins_effects16(g, ws, lv, l, lmo, fcur, fnext, cut_next, c4, low, push, keep, aff);
+                    cnt_l += c4[0] + c4[1] + c4[2] + c4[3];
                     scanned += 4 * (unsigned long long)max(0, min(4, ng - j0));
                     marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
                 }
@@ -1448,13 +1458,7 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
                 for (int q = 0; q < 16; ++q) lv[q] = valid_id(g, ws[q]) ? g.level[ws[q]] : 0;
                 int cl4[4] = {0, 0, 0, 0};
                 unsigned push = 0, keep = 0;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int r = ins_effect(g, ws[q], lv[q], l, lmo, fcur, fnext, cut_next, cl4[q >> 2], low);
-                    if (r & 1) push |= 1u << q;
-                    if (r & 2) keep |= 1u << q;
-                    aff += (r >> 2) & 1;
-                }
+                ins_effects16(g, ws, lv, l, lmo, fcur, fnext, cut_next, cl4, low, push, keep, aff);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) scanned += in[u] ? 4 : 0;
                 marks_add(g, st, push, ws, mbuf, mc, k + 1, wsm);
