@@ -283,10 +283,18 @@ int plds_set_tuning(plds_t *h, const plds_tuning *t);
 int plds_set_wait_limit(plds_t *h, int64_t ns);
 
 /* Diagnostics: per-round records of the last batch call when tuning.trace_rounds
- * is set.  Each record is 12 int32: {level, candidates (insert) or pending entries
- * (delete), movers, thread-mode movers, chunk items, then nanoseconds seen by the
- * first block: insert {phase A work, phase A publish + barrier, phase B work,
- * phase B publish + barrier}, delete {phase 1, phase 2, phase 3}; rest 0}.
+ * is set (single-graph calls).  Each record is 12 int32; times in nanoseconds from
+ * the device clock.  Record 0: {-1 (insert) or -2 (delete), then the durations of
+ * the steps between the rounds kernel's start and its first round}.  Then one per
+ * phase.  Insertion (Algorithm 2): {level, 1 = movers' scan or 0 = test of initial
+ * candidates, movers, thread-mode items, chunk items, first block's work, its
+ * publish + barrier, pure rounds skipped after the phase, latest and earliest end
+ * of a block's work after the phase start, 0, 0}.  Deletion (Algorithm 3): {level,
+ * pending entries, movers, thread-mode items, chunk items, take, apply and
+ * desire-level parts seen by the first block, 0...}.  Jump variant: {level, 2,
+ * movers, large-table movers, pending left, round time, its first part, pure
+ * rounds skipped, staying movers, movers with a non-unit target, lowest other
+ * pending level or -1, lowest non-mover neighbour level or -1}.
  * out holds cap records;
  * returns the number of records written, or a negative PLDS_E* code. */
 int plds_trace(plds_t *h, int32_t *out, int32_t cap);

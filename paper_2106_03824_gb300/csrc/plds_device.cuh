@@ -1545,6 +1545,14 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             if (lane == 0 && low < kInf) atomicMin(&st.ff[2], low);
         }
         const uint64_t t_work = (g.trace && T.leader()) ? global_ns() : 0;
+        if (g.trace) {  // every block: when it finished its share of the phase
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned long long tb = global_ns();
+                atomicMax(&g.ctl->tw_max[k & 1], tb);
+                atomicMax(&g.ctl->tw_min_c[k & 1], ~tb);
+            }
+        }
         stage_flush_round(g, st, 6u);
         if (threadIdx.x == 0) {
             if (*st.movers) {
@@ -1659,7 +1667,12 @@ __device__ bool ins_rounds(Team &T, const GraphCtx &g, const int32_t *sh_upmax, 
             rec[0] = scan ? l2 - 1 : l2; rec[1] = scan ? 1 : 0; rec[2] = m; rec[3] = tlc; rec[4] = clc;
             rec[5] = (int32_t)(t_work - t_phase); rec[6] = (int32_t)(t_end - t_work);
             rec[7] = skip;
-            rec[8] = rec[9] = rec[10] = rec[11] = 0;
+            // blocks' work ends after the phase start: the latest and the earliest
+            rec[8] = (int32_t)(g.ctl->tw_max[k & 1] - t_phase);
+            rec[9] = (int32_t)(~g.ctl->tw_min_c[k & 1] - t_phase);
+            rec[10] = rec[11] = 0;
+            g.ctl->tw_max[k & 1] = 0;
+            g.ctl->tw_min_c[k & 1] = 0;
         }
         if (nm > 0) {
             scan = true;

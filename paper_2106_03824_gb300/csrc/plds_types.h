@@ -95,6 +95,10 @@ struct Ctl {
     unsigned long long c1total;  // chunks of the large shrinking tables' new slots (clear)
     unsigned long long c2total;  // chunks of their live keys (reinsert)
     unsigned long long pool_old;  // pool top before the growing tables took their room
+    // diagnostics (trace mode): per phase parity, the latest and earliest time a block
+    // finished its share of an insertion phase
+    unsigned long long tw_max[2];
+    unsigned long long tw_min_c[2];  // complement of the earliest time (zero means none)
     unsigned long long st[kStCount];
 };
 
