@@ -684,9 +684,9 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
     const Ctl &c = h->host_ctl;
     h->last.err_bits = c.err;
     h->last.err_site = c.err_site;
-        h->last.err_info[0] = c.err_info[0];
-        h->last.err_info[1] = c.err_info[1];
-        h->last.err_info[2] = c.err_info[2];
+    h->last.err_info[0] = c.err_info[0];
+    h->last.err_info[1] = c.err_info[1];
+    h->last.err_info[2] = c.err_info[2];
     h->last.self_loops = (int64_t)c.st[kStSelfLoops];
     h->last.duplicates = B - h->last.self_loops - (int64_t)c.ucount;
     h->last.filtered = (int64_t)c.st[kStFiltered];
