@@ -565,10 +565,11 @@ __device__ void pre_pool_check(Team &T, const GraphCtx &g) {
 }
 
 // Room in the pool for every growing table (after the check), and the
-// work list of the move: every old table cut into chunks of kGrowChunk slots,
+// work list of the move: every old table cut into chunks of kMoveChunk slots,
 // items {growing-table index, chunk} in CL[0].  The rooms are contiguous from the
 // pool top read by the check.
-constexpr int kGrowChunk = 512;
+constexpr int kGrowChunk = 512;  // shrinking: slots per chunk item
+constexpr int kMoveChunk = 128;  // growth: old slots per chunk item (one 16-byte group per lane)
 
 template <class Team>
 __device__ void pre_alloc(Team &T, const GraphCtx &g, unsigned long long *sh) {
@@ -578,7 +579,7 @@ __device__ void pre_alloc(Team &T, const GraphCtx &g, unsigned long long *sh) {
         const int4 it = i < gc ? g.M[0][i] : make_int4(0, 0, 0, 0);
         const unsigned long long off =
             block_reserve<unsigned long long>(g.pool_top, i < gc ? (unsigned long long)it.y : 0ull, sh);
-        const int32_t nch = i < gc ? (g.cap[it.x] + kGrowChunk - 1) / kGrowChunk : 0;
+        const int32_t nch = i < gc ? (g.cap[it.x] + kMoveChunk - 1) / kMoveChunk : 0;
         const unsigned long long c0 = block_reserve<unsigned long long>(&g.ctl->ctotal, (unsigned long long)nch, sh);
         if (i < gc) {
             g.M[0][i] = make_int4(it.x, it.y, (int32_t)(off & 0xffffffffu), (int32_t)(off >> 32));
@@ -610,8 +611,8 @@ __device__ void pre_grow(Team &T, const GraphCtx &g) {
         const int64_t noff = (int64_t)(uint32_t)it.z | ((int64_t)it.w << 32);
         const int32_t oc = g.cap[it.x];
         const int4 *ot = reinterpret_cast<const int4 *>(g.slots + g.off[it.x]);
-        const int j_end = min(oc, (ci.y + 1) * kGrowChunk) >> 2;
-        for (int j = (ci.y * kGrowChunk >> 2) + lane_id(); j < j_end; j += 32) {
+        const int j_end = min(oc, (ci.y + 1) * kMoveChunk) >> 2;
+        for (int j = (ci.y * kMoveChunk >> 2) + lane_id(); j < j_end; j += 32) {
             const int4 q = ot[j];
             if (q.x >= 0) table_insert_fresh(g.slots, noff, it.y, q.x);
             if (q.y >= 0) table_insert_fresh(g.slots, noff, it.y, q.y);
