@@ -207,56 +207,6 @@ def noisy_batch(edges: np.ndarray, n: int, seed: int, self_loops: int = 0,
     return np.ascontiguousarray(out[rng.permutation(out.shape[0])])
 
 
-def chung_lu_device(n: int, m: int, gamma: float, seed: int = 1, device: str = "cuda"):
-    """The chung_lu model drawn on the GPU with a seeded torch generator, for graphs
-    too large for the host generator (billions of endpoint draws).  Same weights,
-    scaling, truncation and stopping rule as chung_lu; returns an int32 [m, 2] tensor
-    on the device, canonical (u < v), unique, ids randomly permuted.  Deterministic
-    for a given seed, device type and PyTorch version (the stream differs from
-    chung_lu's numpy stream)."""
-    import math
-
-    import torch
-    gen = torch.Generator(device=device)
-    gen.manual_seed(int(seed))
-    if n < 2 or m <= 0:
-        return torch.zeros((0, 2), dtype=torch.int32, device=device)
-    w = torch.arange(1, n + 1, dtype=torch.float64, device=device) ** (-1.0 / (gamma - 1.0))
-    cap = math.sqrt(2.0 * m)
-    for _ in range(8):
-        w = torch.clamp(w * (2.0 * m / float(w.sum())), max=cap)
-    cdf = torch.cumsum(w, 0)
-    cdf /= cdf[-1].clone()
-    del w
-    keys = torch.zeros(0, dtype=torch.int64, device=device)
-    drawn = 0
-    chunk = 1 << 27
-    while keys.numel() < m and drawn < 4 * m:
-        rate = drawn / max(keys.numel(), 1) if drawn else 1.2
-        k = int(min(max((m - keys.numel()) * rate * 1.25, 4096), 4 * m - drawn))
-        parts = [keys]
-        for s in range(0, k, chunk):
-            c = min(chunk, k - s)
-            u = torch.searchsorted(cdf, torch.rand(c, generator=gen, device=device, dtype=torch.float64),
-                                   right=True).clamp_(max=n - 1)
-            v = torch.searchsorted(cdf, torch.rand(c, generator=gen, device=device, dtype=torch.float64),
-                                   right=True).clamp_(max=n - 1)
-            keep = u != v
-            u, v = u[keep], v[keep]
-            parts.append(torch.minimum(u, v) * (1 << 32) + torch.maximum(u, v))
-            del u, v, keep
-        drawn += k
-        keys = torch.unique(torch.cat(parts))
-        del parts
-    if keys.numel() > m:
-        keys = keys[torch.randperm(keys.numel(), generator=gen, device=device)[:m]]
-    perm = torch.randperm(n, generator=gen, device=device).to(torch.int32)
-    a = perm[(keys >> 32)]
-    b = perm[(keys & 0xFFFFFFFF)]
-    del keys
-    return torch.stack([torch.minimum(a, b), torch.maximum(a, b)], 1).contiguous()
-
-
 # ---------------------------------------------------------------------------
 # Counter-based Chung-Lu draws: draw k is a pure function of (seed, k), computed in
 # int64 arithmetic whose every intermediate stays below 2^63, so numpy on the host
