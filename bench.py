@@ -1106,7 +1106,7 @@ def main():
                                   "frac": frac(s_rnd),
                                   "definition": "executed work, every move at its degree + 8 B per affected "
                                                 "neighbour"},
-            "batch_sequence": {"kernels": "step kernels (9 per insertion batch, 7 per deletion batch) "
+            "batch_sequence": {"kernels": "step kernels (8 per insertion batch, 6 per deletion batch) "
                                           "+ k_batch_grid, one batch call",
                                "ms_per_batch": kern_ns / 1e6 / nb, "algo_bytes_per_batch": abytes / nb,
                                "achieved": a_seq, "frac": frac(a_seq), "traffic": b_traffic,

@@ -56,16 +56,16 @@ constexpr int kPreThreads = 256;
     FreeTeam T;                 \
     __shared__ unsigned long long sh_res[kPreThreads / 32 + 1]
 
-__global__ void __launch_bounds__(kPreThreads) k_pre_canon(const __grid_constant__ GraphCtx g) {
-    if (ld_volatile(&g.ctl->err)) return;
+__global__ void __launch_bounds__(kPreThreads) k_pre_canon_filter(const __grid_constant__ GraphCtx g) {
     PRE_SCRATCH;
-    pre_canon(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+    pre_canon_filter(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
 }
 
-__global__ void __launch_bounds__(kPreThreads) k_pre_filter(const __grid_constant__ GraphCtx g) {
-    if (ld_volatile(&g.ctl->err)) return;
-    PRE_SCRATCH;
-    pre_filter(T, g, BatchIn{g.edges, g.B, g.op, g.stamp_base}, sh_res);
+// After an insertion batch was rejected for an id outside [0, n): the incoming
+// counts of the touched vertices back to zero (they are per batch).
+__global__ void k_undo_inc(const int32_t *__restrict__ touched, int64_t count, int32_t *inc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        inc[touched[i]] = 0;
 }
 
 __global__ void __launch_bounds__(kPreThreads) k_pre_grow_request(const __grid_constant__ GraphCtx g) {
@@ -565,9 +565,8 @@ static void launch_pre(plds *h, GraphCtx &g) {
     cudaEventRecord(h->ev0, s);
     int k = 0;
     if (g.B > 0) {
-        k_pre_canon<<<blocks, kPreThreads, 0, s>>>(g);
-        k_pre_filter<<<blocks, kPreThreads, 0, s>>>(g);
-        k += 2;
+        k_pre_canon_filter<<<blocks, kPreThreads, 0, s>>>(g);
+        k += 1;
     }
     if (g.op == kOpInsert) {
         k_pre_grow_request<<<blocks, kPreThreads, 0, s>>>(g);
@@ -589,6 +588,17 @@ static void launch_pre(plds *h, GraphCtx &g) {
     cudaEventRecord(h->evm, s);
     h->launches += k;
     g.pre_done = 1;
+}
+
+// An insertion batch rejected for an id outside [0, n) by the one-pass step
+// kernel: its valid keys' incoming counts are cleared, leaving the graph as before.
+static void undo_incoming(plds *h, const Ctl &c, const GraphCtx &g) {
+    if (g.op != kOpInsert || c.ttotal == 0) return;
+    const int64_t cnt = (int64_t)c.ttotal;
+    const int blocks = (int)std::min<int64_t>((cnt + 255) / 256, (int64_t)h->num_sms * 8);
+    k_undo_inc<<<blocks, 256, 0, h->stream>>>(g.touched, cnt, g.inc);
+    h->launches++;
+    cudaStreamSynchronize(h->stream);
 }
 
 static int launch_batch(plds *h, const GraphCtx &g) {
@@ -672,7 +682,10 @@ static int run_op(plds *h, const int32_t *edges, int64_t B, int32_t op) {
             h->poisoned = true;
             return PLDS_ETIMEOUT;
         }
-        if (c.err & kErrInvalidId) return PLDS_EINVAL;
+        if (c.err & kErrInvalidId) {
+            undo_incoming(h, c, g);
+            return PLDS_EINVAL;
+        }
         if (c.err == kErrNeedPool && attempt < 3) {
             rc = grow_pool(h, (int64_t)c.grow_total);
             if (rc) return rc;
@@ -1552,7 +1565,10 @@ extern "C" int plds_batch_static(plds_t *h, const int32_t *edges, int64_t B, int
         h->poisoned = true;
         return set_status(PLDS_ETIMEOUT);
     }
-    if (c.err & kErrInvalidId) return set_status(PLDS_EINVAL);
+    if (c.err & kErrInvalidId) {
+        undo_incoming(h, c, g);
+        return set_status(PLDS_EINVAL);
+    }
     // the adjacency pool is full: growing it would allocate, so report and leave
     // the graph unchanged (a regular plds_batch_insert call can grow it)
     if (c.err == kErrNeedPool) return set_status(PLDS_ENOMEM);

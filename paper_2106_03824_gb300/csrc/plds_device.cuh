@@ -523,6 +523,67 @@ __device__ void pre_filter(Team &T, const GraphCtx &g, const BatchIn &in, unsign
     if (lane_id() == 0 && filtered) atomicAdd(&g.ctl->st[kStFiltered], filtered);
 }
 
+// Step A1 in one pass (the single-graph calls' step kernels): the thread that puts
+// a key into the batch's key set first also filters it, so the unique keys are
+// counted (ucount) but never listed.  An id outside [0, n) anywhere in the batch
+// stops the steps after this one; the incoming counts that valid keys left behind
+// are then cleared (k_undo_inc) before the call reports the error.
+template <class Team>
+__device__ void pre_canon_filter(Team &T, const GraphCtx &g, const BatchIn &in, unsigned long long *sh) {
+    const int2 *e = reinterpret_cast<const int2 *>(in.edges);
+    const int32_t stouch = in.stamp_base;
+    unsigned long long loops = 0, filtered = 0;
+    const int64_t mask = g.hcap - 1, stride = (int64_t)T.nblocks() * blockDim.x;
+    for (int64_t b0 = (int64_t)T.bid() * blockDim.x; b0 < in.B; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool fresh = false;
+        unsigned long long key = 0;
+        int32_t u = 0, v = 0;
+        if (i < in.B) {
+            const int2 uv = e[i];
+            if (uv.x < 0 || uv.x >= g.n || uv.y < 0 || uv.y >= g.n) {
+                atomicOr(&g.ctl->err, kErrInvalidId);
+            } else if (uv.x == uv.y) {
+                loops++;
+            } else {
+                u = min(uv.x, uv.y);
+                v = max(uv.x, uv.y);
+                key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
+                int64_t h = (int64_t)(mix64(key) & (uint64_t)mask);
+                for (int64_t it = 0; it <= mask; ++it) {
+                    const unsigned long long old = atomicCAS(&g.hset[h], kEmptyKey, key);
+                    if (old == kEmptyKey) { fresh = true; break; }
+                    if (old == key) break;
+                    h = (h + 1) & mask;
+                }
+            }
+        }
+        bool keep = false;
+        if (fresh) {
+            const bool present = table_find(g.slots, g.off[u], g.cap[u], v);
+            keep = (in.op == kOpInsert) ? !present : present;
+            if (!keep) filtered++;
+        }
+        block_reserve<unsigned long long>(&g.ctl->ucount, fresh ? 1ull : 0ull, sh);
+        const bool tu = keep && atomicExch(&g.stamp[u], stouch) != stouch;
+        const bool tv = keep && atomicExch(&g.stamp[v], stouch) != stouch;
+        if (keep && in.op == kOpInsert) {
+            atomicAdd(&g.inc[u], 1);
+            atomicAdd(&g.inc[v], 1);
+        }
+        const unsigned long long pos = block_reserve<unsigned long long>(&g.ctl->vcount, keep ? 1ull : 0ull, sh);
+        if (keep) g.vkeys[pos] = key;
+        const unsigned long long pt =
+            block_reserve<unsigned long long>(&g.ctl->ttotal, (unsigned long long)(tu + tv), sh);
+        if (tu) g.touched[pt] = u;
+        if (tv) g.touched[pt + (tu ? 1 : 0)] = v;
+    }
+    loops = warp_sum64(loops);
+    filtered = warp_sum64(filtered);
+    if (lane_id() == 0 && loops) atomicAdd(&g.ctl->st[kStSelfLoops], loops);
+    if (lane_id() == 0 && filtered) atomicAdd(&g.ctl->st[kStFiltered], filtered);
+}
+
 // Step A2 (insert): tables whose load would pass load_num/load_den must grow:
 // list them (M[0] = {x, new size}) and total their sizes.  Run after pre_filter;
 // tcount is taken from its touched total.

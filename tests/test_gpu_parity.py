@@ -312,3 +312,24 @@ def test_bounded_wait_reports_timeout(P):
     o.insert(e)
     assert_same(g2, o, "fresh handle after timeout")
     g2.close()
+
+
+def test_rejected_insertion_leaves_no_trace(P):
+    """A rejected insertion batch whose other edges are new and valid: the next
+    batches grow the tables exactly as on a graph that never saw it (same pool use,
+    same levels and counters as the oracle)."""
+    n = 3000
+    e = W.erdos_renyi(n, 20_000, seed=41)
+    a, b, o = P.PLDS(n), P.PLDS(n), O.OraclePLDS(n)
+    for h in (a, b):
+        h.insert(e[:8000])
+    o.insert(e[:8000])
+    bad = np.concatenate([e[8000:14000], np.array([[5, n + 3]], np.int32)])
+    assert a.insert(bad, check=False) == P.PLDS_EINVAL
+    for h in (a, b):
+        h.insert(e[8000:])
+    o.insert(e[8000:])
+    assert_same(a, o, "after the rejected batch")
+    assert a.stats()["pool_slots_used"] == b.stats()["pool_slots_used"]
+    a.close()
+    b.close()
