@@ -37,3 +37,21 @@ def test_step_bytes_are_part_of_executed_bytes():
     assert bench.algo_bytes_steps(S) == 8000 + 57600
     for kind in ("ins", "del"):
         assert bench.algo_bytes(S, kind) - bench.algo_bytes_steps(S) > 0
+
+
+def test_unique_edges_of_a_raw_pair_stream():
+    """The large form's distinct-edge set of raw draws (CPU tensors here): self-loops
+    dropped, (u, v) and (v, u) one edge, canonical u < v, sorted by key."""
+    torch = __import__("pytest").importorskip("torch")
+    pairs = torch.tensor([[3, 1], [1, 3], [2, 2], [0, 5], [5, 0], [4, 1], [1, 4], [6, 7]], dtype=torch.int32)
+    out = bench.unique_edges_device(pairs)
+    assert out.dtype == torch.int32
+    assert out.tolist() == [[0, 5], [1, 3], [1, 4], [6, 7]]
+
+
+def test_sha_of_int32_arrays_is_little_endian_concatenation():
+    import hashlib
+    import numpy as np
+    a, b = np.array([1, -2], np.int32), np.array([7], np.int64)
+    want = hashlib.sha256(np.array([1, -2, 7], "<i4").tobytes()).hexdigest()
+    assert bench.sha_i32(a, b) == want
