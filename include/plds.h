@@ -71,7 +71,8 @@ typedef struct plds_stats {
     int64_t err_bits;      /* device error word of the last call (diagnostics) */
     int64_t err_site;      /* internal check that raised it (diagnostics) */
     int64_t err_info[3];   /* values seen by that check (diagnostics) */
-    int64_t kernel_ns;     /* device time of the last call's batch kernel (CUDA events) */
+    int64_t kernel_ns;     /* device time of the last call's launch sequence: step kernels and
+                              level-rounds kernel, summed over its attempts (CUDA events) */
     int64_t launches;      /* kernels launched by this handle since creation */
     int64_t up_visits;     /* insertion: up-neighbours of moving vertices, the sum of their
                               up-degrees over the moves (what a move must examine) */
