@@ -108,7 +108,7 @@ def algo_bytes(s: dict, kind: str) -> int:
             + 8 * s["dl_visits"])
 
 
-def algo_bytes_survey(s: dict) -> int:
+def algo_bytes_degree(s: dict) -> int:
     """The same work under the scope table's per-unit figures: per move 4 B (level)
     + 8 B per neighbour of the mover (its degree) + 8 B per neighbour whose counter
     the move changed (affected); per desire-level evaluation 8 B per neighbour;
@@ -1069,7 +1069,7 @@ def main():
     rnd_ns = kern_ns - pre_ns
     abytes = sum(algo_bytes(r, kind) for kind, r in recs)
     pbytes = sum(algo_bytes_steps(r) for _, r in recs)
-    sbytes = sum(algo_bytes_survey(r) for _, r in recs)
+    sbytes = sum(algo_bytes_degree(r) for _, r in recs)
     xbytes = sum(algo_bytes_with_skipped(r, kind) for kind, r in recs)
     peak, peak_src = measured_peaks()
 
@@ -1087,7 +1087,7 @@ def main():
     if args.dump_recs:  # per timed step: algorithmic bytes and durations (matches ncu launch lists)
         with open(args.dump_recs, "w") as f:
             json.dump([{"kind": kind, "algo_bytes": algo_bytes(r, kind), "algo_bytes_steps": algo_bytes_steps(r),
-                        "algo_bytes_survey": algo_bytes_survey(r), "kernel_ns": r["kernel_ns"],
+                        "algo_bytes_degree": algo_bytes_degree(r), "kernel_ns": r["kernel_ns"],
                         "pre_ns": r["pre_ns"], "launches": r["launches"], "valid": r["valid"]}
                        for kind, r in recs], f)
     a_rnd = gbs(abytes - pbytes, rnd_ns)
@@ -1102,7 +1102,7 @@ def main():
             "definition": "executed work of the level rounds: 4 B per level change, 8 B per neighbour "
                           "examined (insertion moves: up-neighbours; deletion moves: all), 8 B per neighbour "
                           "read by a desire-level evaluation; skipped pure rounds left out",
-            "survey_definition": {"algo_bytes_per_launch": (sbytes - pbytes) / nb, "achieved": s_rnd,
+            "degree_definition": {"algo_bytes_per_launch": (sbytes - pbytes) / nb, "achieved": s_rnd,
                                   "frac": frac(s_rnd),
                                   "definition": "executed work, every move at its degree + 8 B per affected "
                                                 "neighbour"},
@@ -1110,8 +1110,8 @@ def main():
                                           "+ k_batch_grid, one batch call",
                                "ms_per_batch": kern_ns / 1e6 / nb, "algo_bytes_per_batch": abytes / nb,
                                "achieved": a_seq, "frac": frac(a_seq), "traffic": b_traffic,
-                               "survey_algo_bytes_per_batch": sbytes / nb, "survey_achieved": s_seq,
-                               "survey_frac": frac(s_seq)},
+                               "degree_algo_bytes_per_batch": sbytes / nb, "degree_achieved": s_seq,
+                               "degree_frac": frac(s_seq)},
             "step_kernels": {"ms_per_batch": pre_ns / 1e6 / nb, "algo_bytes_per_batch": pbytes / nb,
                              "achieved": a_pre, "frac": frac(a_pre),
                              "definition": "8 B per submitted edge + 64 B per applied update"},

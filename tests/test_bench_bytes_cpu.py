@@ -21,9 +21,9 @@ def test_executed_bytes_deletion_uses_degrees():
     assert bench.algo_bytes(S, "del") == 8000 + 57600 + 800 + 8 * 3000 + 480
 
 
-def test_survey_definition():
+def test_degree_definition():
     # per move its degree and its affected neighbours: 8*(7000-4000) + 8*250
-    assert bench.algo_bytes_survey(S) == 8000 + 57600 + 800 + 24000 + 2000 + 480
+    assert bench.algo_bytes_degree(S) == 8000 + 57600 + 800 + 24000 + 2000 + 480
 
 
 def test_with_skipped_rounds():
