@@ -357,6 +357,21 @@ int plds_tune_search(const plds_tuning *start, plds_tune_cost cost, void *ctx, i
                      plds_tuning *best);
 
 /*
+ *   plds_autotune: the search for one handle, on a sample stream: each evaluation
+ *     builds a scratch handle configured like h (n, delta, lambda, levels per
+ *     group, flags, allocator, stream, the other tuning fields), applies batches
+ *     0..nbatches-1 -- batch b is edges[offsets[b] .. offsets[b+1]) (int32 pairs,
+ *     host or device; offsets has nbatches + 1 entries, in edges), an insertion if
+ *     kinds[b] == 0, a deletion if 1 -- and costs the wall time of the batches from
+ *     timed_from on (the earlier ones build the sample's state untimed).  h's graph
+ *     is not touched; its knobs become the best ones (also written to *best when
+ *     non-null).  PLDS_EINVAL on bad arguments; a failing sample batch's code
+ *     otherwise.
+ */
+int plds_autotune(plds_t *h, const int32_t *edges, const int64_t *offsets, const int32_t *kinds, int32_t nbatches,
+                  int32_t timed_from, int32_t max_trials, plds_tuning *best);
+
+/*
  * Serving form: a device-resident request loop over one graph (the paper has no
  * counterpart).  One persistent kernel applies requests from a ring of `slots`
  * slots in pinned host memory, in submission order; coreness queries see the state

@@ -237,6 +237,10 @@ struct plds {
     bool poisoned = false;
     int32_t n = 0;
     bool jump = false;  // insertion: the jump variant (PLDS_FLAG_JUMP)
+    // what plds_create_ex was given (plds_autotune builds scratch handles alike)
+    double delta = 0, lambda = 0;
+    int32_t levels_per_group = 0;
+    uint32_t flags = 0;
     Tables T;
     plds_tuning tune{};
     int64_t wait_limit_ns = 20ll * 1000 * 1000 * 1000;
@@ -758,6 +762,10 @@ plds_t *plds_create_ex(int32_t n, double delta, double lambda, int32_t levels_pe
     }
     h->n = n;
     h->jump = (flags & PLDS_FLAG_JUMP) != 0;
+    h->delta = delta;
+    h->lambda = lambda;
+    h->levels_per_group = levels_per_group;
+    h->flags = flags;
     const size_t N = (size_t)n;
     const size_t G = (size_t)h->T.G, K = (size_t)h->T.K;
     h->pool_cap = std::max<int64_t>(1 << 20, 8 * (int64_t)n);
@@ -2030,6 +2038,76 @@ extern "C" int plds_set_autotune(plds_set_t *s, int32_t rounds, const int32_t *c
     const int rc = plds_set_tune(s, &out);
     if (rc) return rc;
     if (best) *best = out;
+    return set_status(PLDS_OK);
+}
+
+namespace {
+struct HandleTuneCtx {
+    plds *h;
+    const int32_t *edges;
+    const int64_t *offsets;
+    const int32_t *kinds;
+    int32_t nbatches, timed_from;
+    int status;
+};
+
+// One evaluation: a scratch handle configured like the handle being tuned, the
+// sample batches applied to it, the wall time of the timed ones (each call is
+// synchronous).
+double handle_trial_cost(const plds_tuning *t, void *ctx) {
+    auto *c = static_cast<HandleTuneCtx *>(ctx);
+    plds *h = c->h;
+    plds *x = plds_create_ex(h->n, h->delta, h->lambda, h->levels_per_group, h->custom_alloc ? &h->alloc : nullptr,
+                             (void *)h->stream, h->flags);
+    if (!x) {
+        c->status = plds_last_status();
+        return -1.0;
+    }
+    plds_tuning tt = h->tune;
+    tt.thread_max_cap = t->thread_max_cap;
+    tt.block_cap = t->block_cap;
+    tt.load_num = t->load_num;
+    tt.load_den = t->load_den;
+    tt.list_cap = t->list_cap;
+    tt.trace_rounds = 0;
+    tt.track_orientation = 0;
+    int rc = plds_set_tuning(x, &tt);
+    double secs = 0.0;
+    for (int32_t b = 0; b < c->nbatches && rc == PLDS_OK; ++b) {
+        const int32_t *e = c->edges + 2 * c->offsets[b];
+        const int64_t B = c->offsets[b + 1] - c->offsets[b];
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = c->kinds[b] ? plds_batch_delete(x, e, B) : plds_batch_insert(x, e, B);
+        if (b >= c->timed_from) secs += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    plds_destroy(x);
+    if (rc != PLDS_OK) {
+        c->status = rc;
+        return -1.0;
+    }
+    return secs;
+}
+}  // namespace
+
+extern "C" int plds_autotune(plds_t *h, const int32_t *edges, const int64_t *offsets, const int32_t *kinds,
+                             int32_t nbatches, int32_t timed_from, int32_t max_trials, plds_tuning *best) {
+    if (!h || !edges || !offsets || !kinds || nbatches < 1 || timed_from < 0 || timed_from >= nbatches ||
+        max_trials < 1)
+        return set_status(PLDS_EINVAL);
+    if (h->poisoned) return set_status(PLDS_EPOISONED);
+    for (int32_t b = 0; b < nbatches; ++b)
+        if (offsets[b] < 0 || offsets[b + 1] < offsets[b] || (kinds[b] != 0 && kinds[b] != 1))
+            return set_status(PLDS_EINVAL);
+    HandleTuneCtx c{h, edges, offsets, kinds, nbatches, timed_from, PLDS_OK};
+    plds_tuning out{};
+    const int trials = plds_tune_search(&h->tune, handle_trial_cost, &c, max_trials, &out);
+    if (trials < 0) return set_status(c.status != PLDS_OK ? c.status : trials);
+    h->tune.thread_max_cap = out.thread_max_cap;
+    h->tune.block_cap = out.block_cap;
+    h->tune.load_num = out.load_num;
+    h->tune.load_den = out.load_den;
+    h->tune.list_cap = out.list_cap;
+    if (best) *best = h->tune;
     return set_status(PLDS_OK);
 }
 

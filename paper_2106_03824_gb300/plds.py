@@ -116,6 +116,7 @@ def load():
     L.plds_set_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                     i32, i32, ctypes.POINTER(PldsTuning)]
     L.plds_tune_search.argtypes = [ctypes.POINTER(PldsTuning), TUNE_COST, vp, i32, ctypes.POINTER(PldsTuning)]
+    L.plds_autotune.argtypes = [vp, vp, vp, vp, i32, i32, i32, ctypes.POINTER(PldsTuning)]
     L.plds_server_create.restype = vp
     L.plds_server_create.argtypes = [vp, i32, i64]
     L.plds_server_submit.argtypes = [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_int64)]
@@ -283,6 +284,27 @@ class PLDS:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(load().plds_set_tuning(self._h, ctypes.byref(t)), "plds_set_tuning")
+
+    def autotune(self, batches, timed_from: int = 1, max_trials: int = 12) -> dict:
+        """Pick this handle's speed-only knobs on a sample stream applied to scratch
+        handles built alike: batches = [(kind, edges)] with kind "ins" or "del" and
+        edges int32 [B, 2] (host arrays, or device tensors for representative
+        timings), the ones before timed_from untimed.  The graph is not touched;
+        the best knobs are applied and returned."""
+        edges = [self._edges(e) for _, e in batches]
+        offs = np.zeros(len(edges) + 1, np.int64)
+        offs[1:] = np.cumsum([e.shape[0] for e in edges])
+        kinds = np.array([0 if k == "ins" else 1 for k, _ in batches], np.int32)
+        if all(isinstance(e, np.ndarray) for e in edges):
+            flat = np.ascontiguousarray(np.concatenate(edges) if edges else np.zeros((0, 2), np.int32))
+        else:
+            torch = __import__("torch")
+            flat = torch.cat([torch.as_tensor(e).to(edges[0].device) for e in edges]).contiguous()
+        best = PldsTuning()
+        rc = load().plds_autotune(self._h, _ptr(flat), _ptr(offs), _ptr(kinds), len(edges), int(timed_from),
+                                  int(max_trials), ctypes.byref(best))
+        self._check(rc, "plds_autotune")
+        return best.knobs()
 
     def static_coreness(self, eps_prime: float = 1.0, out=None):
         """Static (2+eps')-approximate k-core of the current graph (Algorithm 6):

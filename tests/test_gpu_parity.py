@@ -333,3 +333,28 @@ def test_rejected_insertion_leaves_no_trace(P):
     assert a.stats()["pool_slots_used"] == b.stats()["pool_slots_used"]
     a.close()
     b.close()
+
+
+def test_single_handle_autotune(P):
+    """plds_autotune on a sample stream: the handle's graph is untouched, the knobs
+    picked are candidates of the search, and results with them still equal the
+    oracle's."""
+    n = 20_000
+    e = W.shuffled(W.chung_lu(n, 100_000, 2.3, seed=12), 3)
+    g, o = P.PLDS(n), O.OraclePLDS(n)
+    g.insert(e[:40_000])
+    o.insert(e[:40_000])
+    before = g.levels().copy()
+    sample = [("ins", e[:30_000]), ("ins", torch.from_numpy(e[30_000:60_000]).cuda()), ("del", e[:10_000])]
+    knobs = g.autotune(sample, timed_from=1, max_trials=6)
+    assert np.array_equal(g.levels(), before)
+    assert knobs["thread_max_cap"] in (4, 8, 16, 32, 64)
+    assert knobs["block_cap"] in (1024, 2048, 4096, 8192, 16384)
+    assert (knobs["load_num"], knobs["load_den"]) in ((1, 2), (5, 8), (3, 4), (7, 8))
+    g.insert(e[40_000:])
+    o.insert(e[40_000:])
+    assert_same(g, o, "after autotune")
+    g.delete(e[::2])
+    o.delete(e[::2])
+    assert_same(g, o, "after autotune, deletions")
+    g.close()
