@@ -1877,6 +1877,37 @@ __device__ int32_t warp_desire_level(const GraphCtx &g, int32_t w, int32_t lw, c
     const int32_t ng = g.cap[w] >> 2;
     const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
     const int32_t xmax = lw - 2;
+    if (ng <= 128) {
+        // The whole table in registers (four 16-byte groups per lane): the answer by
+        // bisection on the definition's predicate P(x) = cnt(x) >= dnmin[gn(x)],
+        // which holds for every x up to the answer's level and for none above (cnt
+        // does not rise with x, dnmin does not fall), each cnt(x) one warp sum.
+        int32_t lvv[16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = lane + 32 * u;
+            const int4 q = j < ng ? t4[j] : empty4();
+            lvv[4 * u] = q.x >= 0 ? g.level[q.x] : -1;
+            lvv[4 * u + 1] = q.y >= 0 ? g.level[q.y] : -1;
+            lvv[4 * u + 2] = q.z >= 0 ? g.level[q.z] : -1;
+            lvv[4 * u + 3] = q.w >= 0 ? g.level[q.w] : -1;
+        }
+        auto cnt_ge = [&](int32_t x) {
+            int c = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) c += lvv[k] >= x ? 1 : 0;
+            return (int32_t)__reduce_add_sync(kFull, (unsigned)c);
+        };
+        if (cnt_ge(0) < sh_dnmin[0]) return 0;
+        int32_t lo = 0, hi = xmax + 1;  // P(lo) holds; P(hi) is taken as false
+        while (hi - lo > 1) {
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if (cnt_ge(mid) >= sh_dnmin[mid / Lg]) lo = mid;
+            else hi = mid;
+        }
+        *slack = cnt_ge(lo) - sh_dnmin[lo / Lg];
+        return lo + 1;
+    }
     const int32_t w0 = max(0, xmax - (kWindow - 1));
     int32_t *win = hist + G;  // levels w0..xmax one by one, win[kWindow]: above xmax
     const bool one = G + kWindow + 1 <= kWarpHist;
