@@ -286,7 +286,9 @@ int plds_set_wait_limit(plds_t *h, int64_t ns);
 /* Diagnostics: per-round records of the last batch call when tuning.trace_rounds
  * is set (single-graph calls).  Each record is 12 int32; times in nanoseconds from
  * the device clock.  Record 0: {-1 (insert) or -2 (delete), then the durations of
- * the steps between the rounds kernel's start and its first round}.  Then one per
+ * the steps between the rounds kernel's start and its first round; for a deletion
+ * batch, entries 8-10 hold the touched vertices and how many of them took a
+ * desire-level computation by a warp and by a block}.  Then one per
  * phase.  Insertion (Algorithm 2): {level, 1 = movers' scan or 0 = test of initial
  * candidates, movers, thread-mode items, chunk items, first block's work, its
  * publish + barrier, pure rounds skipped after the phase, latest and earliest end

@@ -2041,6 +2041,58 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
     }
 }
 
+// Desire-level of a vertex whose table has at most kThreadDl slots, by one thread:
+// its neighbours' levels in registers, bisection on P(x) = cnt(x) >= dnmin[gn(x)]
+// as in warp_desire_level.
+constexpr int kThreadDl = 16;
+
+__device__ __forceinline__ int32_t thread_desire_level(const GraphCtx &g, int32_t w, int32_t lw, int32_t c,
+                                                       const int32_t *sh_dnmin, int32_t *slack) {
+    *slack = kInf;
+    if (lw < 2) return 0;
+    const int4 *t4 = reinterpret_cast<const int4 *>(g.slots + g.off[w]);
+    const int ng = c >> 2;
+    int32_t lvv[kThreadDl];
+#pragma unroll
+    for (int u = 0; u < kThreadDl / 4; ++u) {
+        const int4 q = u < ng ? t4[u] : empty4();
+        lvv[4 * u] = q.x >= 0 ? g.level[q.x] : -1;
+        lvv[4 * u + 1] = q.y >= 0 ? g.level[q.y] : -1;
+        lvv[4 * u + 2] = q.z >= 0 ? g.level[q.z] : -1;
+        lvv[4 * u + 3] = q.w >= 0 ? g.level[q.w] : -1;
+    }
+    auto cnt_ge = [&](int32_t x) {
+        int32_t n = 0;
+#pragma unroll
+        for (int k = 0; k < kThreadDl; ++k) n += lvv[k] >= x ? 1 : 0;
+        return n;
+    };
+    if (cnt_ge(0) < sh_dnmin[0]) return 0;
+    int32_t lo = 0, hi = lw - 1;  // P(lo) holds; P(hi) is taken as false (answers stop at lw - 2)
+    while (hi - lo > 1) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (cnt_ge(mid) >= sh_dnmin[mid / g.Lg]) lo = mid;
+        else hi = mid;
+    }
+    *slack = cnt_ge(lo) - sh_dnmin[lo / g.Lg];
+    return lo + 1;
+}
+
+// A desire-level d computed for w (slack sl): recorded, and a pending entry in
+// P[q] unless it equals w's current pending level.
+__device__ __forceinline__ void dl_record(const GraphCtx &g, int32_t w, int32_t d, int32_t sl, int q, int32_t lmin,
+                                          int site) {
+    g.dslack[w] = sl;
+    if (d <= lmin) {
+        report(g, kErrInternal, site, w, d, lmin);
+    } else if (d != g.dlv[w]) {
+        g.dlv[w] = d;
+        const int pos = atomicAdd(&g.ctl->pcnt[q], 1);
+        g.P[q][pos] = make_int4(w, d, 0, 0);
+        atomicMin(&g.ctl->nextmin[q], d);
+    }
+}
+
 // Desire-levels for every vertex of src[0..count) that violates Invariant 2
 // (level > 0 and up* < dnmin[gn(level-1)]).  Two phases with a team barrier:
 // classify into a warp list (small tables, from the front of RL) and a block list
@@ -2070,6 +2122,14 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
                 evals++;
                 evisits += g.deg[w];
             }
+            if (viol && c <= kThreadDl) {  // a small table: this thread computes it
+                viol = false;
+                int32_t sl;
+                const int32_t d = thread_desire_level(g, w, lw, c, sh_dnmin, &sl);
+                evals++;
+                evisits += g.deg[w];
+                dl_record(g, w, d, sl, q, lmin, 10);
+            }
         }
         const int pw = warp_append(&g.ctl->rcnt[1], viol && !big);
         if (viol && !big) RL[pw] = w;
@@ -2083,17 +2143,9 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
         int32_t sl;
         const int32_t d = warp_desire_level(g, w, lw, sh_dnmin, whist, &sl);
         if (lane == 0) {
-            g.dslack[w] = sl;
             evals++;
             evisits += g.deg[w];
-            if (d <= lmin) {
-                report(g, kErrInternal, 8, w, d, lmin);
-            } else if (d != g.dlv[w]) {
-                g.dlv[w] = d;
-                const int pos = atomicAdd(&g.ctl->pcnt[q], 1);
-                g.P[q][pos] = make_int4(w, d, 0, 0);
-                atomicMin(&g.ctl->nextmin[q], d);
-            }
+            dl_record(g, w, d, sl, q, lmin, 8);
         }
     }
     for (int i = T.bid(); i < nb; i += (T.nthreads() / blockDim.x)) {
@@ -2101,17 +2153,9 @@ __device__ bool dl_batch(Team &T, const GraphCtx &g, const int32_t *src, int32_t
         int32_t sl;
         const int32_t d = block_desire_level(g, w, lw, sh_dnmin, bhist, bhist + kWarpHist, &sl);
         if (threadIdx.x == 0) {
-            g.dslack[w] = sl;
             evals++;
             evisits += g.deg[w];
-            if (d <= lmin) {
-                report(g, kErrInternal, 9, w, d, lmin);
-            } else if (d != g.dlv[w]) {
-                g.dlv[w] = d;
-                const int pos = atomicAdd(&g.ctl->pcnt[q], 1);
-                g.P[q][pos] = make_int4(w, d, 0, 0);
-                atomicMin(&g.ctl->nextmin[q], d);
-            }
+            dl_record(g, w, d, sl, q, lmin, 9);
         }
     }
     return true;
@@ -2877,6 +2921,9 @@ __device__ void run_batch(Team &T, const GraphCtx &g, const BatchIn &in, int32_t
         if (tr) {
             tmark[nmark++] = global_ns();
             trace_steps(g, tmark, nmark, -2);
+            g.trace[8] = g.ctl->tcount;   // vertices the batch touched
+            g.trace[9] = g.ctl->rcnt[1];  // of them violating, desire-level by a warp
+            g.trace[10] = g.ctl->rbcnt;   // by a block (tables above block_cap)
         }
         if (T.leader()) {
             g.ctl->rcnt[1] = 0;
