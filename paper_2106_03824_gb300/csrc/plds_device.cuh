@@ -2044,7 +2044,7 @@ __device__ int32_t block_desire_level(const GraphCtx &g, int32_t w, int32_t lw, 
 // Desire-level of a vertex whose table has at most kThreadDl slots, by one thread:
 // its neighbours' levels in registers, bisection on P(x) = cnt(x) >= dnmin[gn(x)]
 // as in warp_desire_level.
-constexpr int kThreadDl = 16;
+constexpr int kThreadDl = 32;
 
 __device__ __forceinline__ int32_t thread_desire_level(const GraphCtx &g, int32_t w, int32_t lw, int32_t c,
                                                        const int32_t *sh_dnmin, int32_t *slack) {
