@@ -294,7 +294,8 @@ int plds_set_wait_limit(plds_t *h, int64_t ns);
  * publish + barrier, pure rounds skipped after the phase, latest and earliest end
  * of a block's work after the phase start, 0, 0}.  Deletion (Algorithm 3): {level,
  * pending entries, movers, thread-mode items, chunk items, take, apply and
- * desire-level parts seen by the first block, 0...}.  Jump variant: {level, 2,
+ * desire-level parts seen by the first block, desire-levels computed by a warp and
+ * by a block after the classifying pass, 0, 0}.  Jump variant: {level, 2,
  * movers, large-table movers, pending left, round time, its first part, pure
  * rounds skipped, staying movers, movers with a non-unit target, lowest other
  * pending level or -1, lowest non-mover neighbour level or -1}.

@@ -2388,7 +2388,9 @@ __device__ bool del_rounds(Team &T, const GraphCtx &g, const int32_t stamp_base,
             rec[0] = l; rec[1] = pc; rec[2] = tr_movers; rec[3] = tlc; rec[4] = clc;
             rec[5] = (int32_t)(t_mid1 - t_round); rec[6] = (int32_t)(t_mid2 - t_mid1);
             rec[7] = (int32_t)(t_end - t_mid2);
-            rec[8] = rec[9] = rec[10] = rec[11] = 0;
+            rec[8] = g.ctl->rcnt[1];  // desire-levels computed by a warp after the classifying pass
+            rec[9] = g.ctl->rbcnt;    // and by a block
+            rec[10] = rec[11] = 0;
         }
     }
     visits = warp_sum64(visits);
