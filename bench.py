@@ -54,7 +54,7 @@ UNIT = "updates/s"
 # DRAM bytes per algorithmic byte, from an ncu counter capture of the timed steps'
 # kernels (profiles/traffic_rmat20_B1e6.md); valid only for the kernel sources it was
 # taken on (kernel_sha), otherwise `traffic` is reported as null.
-NCU_TRAFFIC = {"kernel_sha": "3d3bd5b065481a78", "rounds_dram_per_algo_byte": 0.670,
+NCU_TRAFFIC = {"kernel_sha": "c837abe3941c36e1", "rounds_dram_per_algo_byte": 0.670,
                "batch_dram_per_algo_byte": 2.158,
                "capture": "ncu DRAM counters of every kernel of the timed steps of the R-MAT 20 stream, "
                           "Ins 14-15 and Del 0-1 (profiles/traffic_rmat20_B1e6.md)"}
