@@ -44,6 +44,13 @@ def test_invalid_parameters_rejected_without_device(lib):
         assert lib.plds_last_status() == P.PLDS_EINVAL
     assert lib.plds_batch_insert(None, None, 0) == P.PLDS_EINVAL
     assert lib.plds_levels(None, None) == P.PLDS_EINVAL
+    # the single-handle autotuner checks its arguments first as well
+    offs = np.array([0, 1], np.int64)
+    kinds = np.array([0], np.int32)
+    e = np.zeros((1, 2), np.int32)
+    best = P.PldsTuning()
+    assert lib.plds_autotune(None, e.ctypes.data, offs.ctypes.data, kinds.ctypes.data, 1, 0, 4,
+                             ctypes.byref(best)) == P.PLDS_EINVAL
 
 
 def test_serving_admission_rule(lib):
