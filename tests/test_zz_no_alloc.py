@@ -69,6 +69,27 @@ def test_static_rejects_oversized_batches(P):
     g.close()
 
 
+def test_static_rejected_ids_leave_no_trace(P):
+    """A static insertion batch with an id outside [0, n) among new valid edges is
+    rejected; the next static batches grow the tables and give the results of a
+    handle that never saw it."""
+    n = 3000
+    e = W.erdos_renyi(n, 20_000, seed=43)
+    a, b = P.PLDS(n), P.PLDS(n)
+    for h in (a, b):
+        assert _static(P, h, e[:8000], 0) == P.PLDS_OK
+    bad = np.concatenate([e[8000:14000], np.array([[7, n]], np.int32)])
+    assert _static(P, a, bad, 0) == P.PLDS_EINVAL
+    for h in (a, b):
+        assert _static(P, h, e[8000:], 0) == P.PLDS_OK
+    assert np.array_equal(a.levels(), b.levels())
+    for x, y in zip(a.counters(), b.counters()):
+        assert np.array_equal(x, y)
+    assert a.stats()["pool_slots_used"] == b.stats()["pool_slots_used"]
+    a.close()
+    b.close()
+
+
 def _counting_handle(P, n):
     """A handle whose device memory comes from a counting allocator callback."""
     L = P.load()
